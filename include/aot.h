@@ -1,0 +1,173 @@
+/*
+ * aot.h - C ABI of the GB300 AOT triangle engine (libaot.so).
+ *
+ * AOT (adaptive orientation triangle listing) lists every triangle of an
+ * undirected simple graph exactly once (problem statement of Sec. 2.1) with
+ * the edge iterator of Algorithm 3: the graph is oriented along a global
+ * order eta (Sec. 1, Sec. 2.2), and each oriented edge <u,v> is charged to
+ * the endpoint with the larger out-degree, whose out-neighbour index H is
+ * probed by the out-list of the other endpoint (Sec. 3.1, Sec. 3.2), for
+ * Theta(sum over <u,v> of min{deg+(u), deg+(v)}) work (Sec. 3.2).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are DEVICE pointers (the current CUDA device); h_*
+ *    are HOST pointers.  Vertex ids are int32 in [0, n).
+ *  - Ownership: the caller owns every buffer.  The library never calls
+ *    cudaMalloc or cudaFree; sizes of the device workspaces it needs are
+ *    reported by the *_workspace_size queries, and the workspace must stay
+ *    alive and untouched while a graph handle that points into it is used.
+ *    The only host allocation is the small aot_graph handle.
+ *  - Streams: every call is ordered on the given stream (NULL = legacy
+ *    default stream).  A call that returns a host value (h_*) synchronises
+ *    that stream before it returns.
+ *  - Errors: every entry point returns an aot_status and never aborts or
+ *    traps.  Bad input found on the device (a vertex id outside [0, n))
+ *    raises a device error word that the call reads back before returning.
+ *    After AOT_ERR_CUDA the CUDA context may be unusable.
+ *  - Thread safety: a graph handle must not be used by two host threads at
+ *    once; distinct handles are independent.
+ */
+#ifndef AOT_H
+#define AOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so that this header does not need
+ * the CUDA runtime headers. */
+typedef struct CUstream_st* aot_stream_t;
+
+typedef enum {
+  AOT_OK = 0,
+  AOT_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, unknown flag   */
+  AOT_ERR_VERTEX_RANGE = 2, /* an input id lies outside [0, n)             */
+  AOT_ERR_OVERFLOW = 3,     /* a size exceeds the index types (see below)  */
+  AOT_ERR_WORKSPACE = 4,    /* workspace too small or not 256-byte aligned */
+  AOT_ERR_CUDA = 5,         /* a CUDA runtime call failed                  */
+  AOT_ERR_TIMEOUT = 6,      /* a bounded device wait ran out               */
+  AOT_ERR_DEVICE_CHECK = 7, /* a device-side consistency check failed      */
+  AOT_ERR_NOT_READY = 8     /* e.g. learned routing without router weights */
+} aot_status;
+
+/* How oriented edges are assigned to intersection variants.  The output never
+ * depends on the route: every variant finds the same triangles. */
+typedef enum {
+  AOT_ROUTE_PLAIN = 0,   /* Algorithm 3: every edge probes its pivot's index */
+  AOT_ROUTE_LEARNED = 1, /* the MLP router chooses a variant per edge        */
+  AOT_ROUTE_PROBE = 2,   /* fixed: pivot index probe (same as PLAIN)         */
+  AOT_ROUTE_MERGE = 3,   /* fixed: warp merge of the two sorted lists        */
+  AOT_ROUTE_BSEARCH = 4, /* fixed: binary search of each walked entry        */
+  AOT_ROUTE_RANDOM = 5   /* test only: seeded random variant per edge        */
+} aot_route;
+
+/* Orientation flags (aot_orient).  The global order eta of Sec. 1: */
+#define AOT_ETA_DEG_DESC 0x0u /* degree non-increasing, ties by smaller id (default) */
+#define AOT_ETA_DEG_ASC 0x1u  /* degree non-decreasing, ties by smaller id           */
+#define AOT_FLAG_NO_LIST 0x2u /* size the workspace without the listing arrays      */
+
+/* Size limits: n < 2^31, num_edges < 2^40, oriented edges m < 2^32.  Larger
+ * inputs return AOT_ERR_OVERFLOW. */
+
+typedef struct aot_graph aot_graph; /* opaque host handle */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* aot_status_string(aot_status status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int aot_version(void);
+
+/* Device workspace bytes that aot_orient needs for an input of num_edges
+ * pairs over num_vertices ids with the given flags (an upper bound: it does
+ * not depend on the edge values). */
+aot_status aot_orient_workspace_size(int64_t num_edges, int32_t num_vertices, uint32_t flags,
+                                     size_t* bytes);
+
+/* Orientation (Algorithm 3, first step; local order of Sec. 3.2):
+ *  1. cleanup: drop self-loops, merge duplicate and reversed pairs (the input
+ *     is treated as an undirected simple graph, Sec. 2.1);
+ *  2. eta: rank vertices by degree (flags), ties by smaller id (footnote of
+ *     the correctness argument in Sec. 3.2);
+ *  3. oriented out-CSR in rank space, every out-list sorted by eta;
+ *  4. the work items of Algorithm 3: an edge <u,v> becomes a positive item of
+ *     pivot u walking N+(v) when key(v) < key(u), else a negative item of
+ *     pivot v walking the part of N+(u) after v (key = (deg+, rank));
+ *  5. degree bins of the pivots for the intersection kernels.
+ * d_src, d_dst: num_edges int32 endpoint pairs (any direction).
+ * d_workspace: >= aot_orient_workspace_size bytes, 256-byte aligned.
+ * On success *out receives a new handle (free it with aot_graph_destroy).
+ * Synchronises s.  Errors: AOT_ERR_VERTEX_RANGE if an id is outside [0, n). */
+aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int64_t num_edges,
+                      int32_t num_vertices, uint32_t flags, void* d_workspace, size_t ws_bytes,
+                      aot_stream_t s, aot_graph** out);
+
+/* Host-side facts of an oriented graph: n, m (= undirected simple edges =
+ * oriented edges), W = summed walk length of Algorithm 3 (the work counter
+ * of the Sec. 3.2 analysis, with negative walks clipped after the pivot),
+ * S = summed deg+ of the pivots that own at least one item (index staging),
+ * max_outdeg = max deg+.  Any pointer may be NULL. */
+aot_status aot_graph_info(const aot_graph* g, int32_t* n, int64_t* m, uint64_t* work_w,
+                          uint64_t* staged_s, int32_t* max_outdeg);
+
+/* Copy the orientation into caller buffers (any pointer may be NULL):
+ * d_perm[n] (eta position -> original id), d_rank[n] (original id -> eta
+ * position), d_out_off[n+1] (uint32 offsets of the out-CSR, rank space),
+ * d_out_adj[m] (uint32 heads, ascending inside each list),
+ * d_items[n] (uint32 number of work items per pivot), d_walk[n] (uint64
+ * summed walk length per pivot).  Ordered on s (no sync). */
+aot_status aot_graph_export(const aot_graph* g, int32_t* d_perm, int32_t* d_rank,
+                            uint32_t* d_out_off, uint32_t* d_out_adj, uint32_t* d_items,
+                            uint64_t* d_walk, aot_stream_t s);
+
+/* Triangle count T (Sec. 5: listing solves counting).  Synchronises s. */
+aot_status aot_count(aot_graph* g, aot_route route, uint64_t* h_total, aot_stream_t s);
+
+/* Per-vertex counts t(v) = triangles containing v, written to d_counts[n]
+ * (uint64, ORIGINAL ids; overwritten).  sum t(v) = 3T.  h_total may be NULL
+ * (then the call does not synchronise). */
+aot_status aot_count_per_vertex(aot_graph* g, aot_route route, uint64_t* d_counts,
+                                uint64_t* h_total, aot_stream_t s);
+
+/* Listing by count, exclusive scan, write.  Triangles are numbered in the
+ * canonical order: (x,y,z) with eta(x) < eta(y) < eta(z), sorted by
+ * (eta(x), eta(y), eta(z)).  This call writes triangles [cursor, cursor+k)
+ * with k = min(cap, T - cursor) to d_out (3*cap int32, ORIGINAL ids, x y z
+ * per triangle), and returns k in *h_written and cursor + k in *h_next (== T
+ * when done).  The first call on a graph runs the count and scan passes; the
+ * per-edge offsets are kept in the workspace for later chunks.  Needs a
+ * workspace sized without AOT_FLAG_NO_LIST.  Synchronises s. */
+aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_out,
+                    uint64_t cap, uint64_t* h_written, uint64_t* h_next, aot_stream_t s);
+
+/* Launch tuning of the intersection kernels.  Pivots are binned by deg+:
+ * deg+ <= warp_max_outdeg -> one warp per pivot (hash table in the warp's
+ * shared memory; warp_max_outdeg <= 64), deg+ <= cta_max_outdeg -> one CTA
+ * per pivot (shared-memory hash table; cta_max_outdeg <= 8192), larger ->
+ * hub path (global bitmaps of n bits, hub_bitmaps of them at a time, 1..64).
+ * cta_threads is a multiple of 32 in [64, 1024].  Tuning never changes
+ * results, only speed. */
+typedef struct {
+  uint32_t warp_max_outdeg;
+  uint32_t cta_max_outdeg;
+  int32_t cta_threads;
+  int32_t hub_bitmaps;
+} aot_tuning;
+
+/* Current tuning of a graph (defaults after aot_orient). */
+aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t);
+
+/* Set the tuning and re-bin the pivots (synchronises s).  Out-of-range values
+ * return AOT_ERR_INVALID_ARG and leave the graph unchanged.  hub_bitmaps may
+ * not exceed the value the workspace was sized for (32). */
+aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t s);
+
+/* Free the host handle (the workspace stays with the caller). */
+aot_status aot_graph_destroy(aot_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AOT_H */

@@ -1,0 +1,82 @@
+// aot_api.cu - small C-ABI entry points: status strings, graph facts, export,
+// destroy.  The heavy entry points live next to their kernels.
+#include "aot_internal.cuh"
+
+using namespace aot;
+
+extern "C" const char* aot_status_string(aot_status st) {
+  switch (st) {
+    case AOT_OK: return "ok";
+    case AOT_ERR_INVALID_ARG: return "invalid argument";
+    case AOT_ERR_VERTEX_RANGE: return "vertex id outside [0, n)";
+    case AOT_ERR_OVERFLOW: return "size exceeds the supported index range";
+    case AOT_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case AOT_ERR_CUDA: return "CUDA runtime error";
+    case AOT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AOT_ERR_DEVICE_CHECK: return "device consistency check failed";
+    case AOT_ERR_NOT_READY: return "not ready (missing router weights or unsupported route)";
+  }
+  return "unknown status";
+}
+
+extern "C" int aot_version(void) { return 100; }
+
+extern "C" aot_status aot_graph_info(const aot_graph* g, int32_t* n, int64_t* m, uint64_t* work_w,
+                                     uint64_t* staged_s, int32_t* max_outdeg) {
+  if (!g) return AOT_ERR_INVALID_ARG;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (work_w) *work_w = g->W;
+  if (staged_s) *staged_s = g->S;
+  if (max_outdeg) *max_outdeg = g->max_outdeg;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_graph_export(const aot_graph* g, int32_t* d_perm, int32_t* d_rank,
+                                       uint32_t* d_out_off, uint32_t* d_out_adj, uint32_t* d_items,
+                                       uint64_t* d_walk, aot_stream_t stream) {
+  if (!g) return AOT_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)g->n, m = (size_t)g->m;
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> aot_status {
+    if (dst && bytes) AOT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    return AOT_OK;
+  };
+  AOT_TRY(cp(d_perm, g->perm, n * sizeof(int32_t)));
+  AOT_TRY(cp(d_rank, g->rank, n * sizeof(int32_t)));
+  AOT_TRY(cp(d_out_off, g->off, (n + 1) * sizeof(uint32_t)));
+  AOT_TRY(cp(d_out_adj, g->adj, m * sizeof(uint32_t)));
+  AOT_TRY(cp(d_items, g->items, n * sizeof(uint32_t)));
+  AOT_TRY(cp(d_walk, g->walk, n * sizeof(uint64_t)));
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
+  if (!g || !t) return AOT_ERR_INVALID_ARG;
+  t->warp_max_outdeg = g->tune.warp_max_outdeg;
+  t->cta_max_outdeg = g->tune.cta_max_outdeg;
+  t->cta_threads = g->tune.cta_threads;
+  t->hub_bitmaps = g->tune.hub_bitmaps;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t stream) {
+  if (!g || !t) return AOT_ERR_INVALID_ARG;
+  if (t->warp_max_outdeg > 64 || t->cta_max_outdeg > 8192 ||
+      t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
+      (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps)
+    return AOT_ERR_INVALID_ARG;
+  Tuning old = g->tune;
+  g->tune.warp_max_outdeg = t->warp_max_outdeg;
+  g->tune.cta_max_outdeg = t->cta_max_outdeg;
+  g->tune.cta_threads = t->cta_threads;
+  g->tune.hub_bitmaps = t->hub_bitmaps;
+  aot_status st = bin_pivots(g, reinterpret_cast<cudaStream_t>(stream));
+  if (st != AOT_OK) g->tune = old;
+  return st;
+}
+
+extern "C" aot_status aot_graph_destroy(aot_graph* g) {
+  delete g;
+  return AOT_OK;
+}

@@ -1,0 +1,521 @@
+// aot_count.cu - the walk-and-probe core of Algorithm 3 on the GPU.
+//
+// Every pivot p builds its index H over N+(p) once (Algorithm 3, index set-up
+// per pivot; Sec. 3.2 stresses that each vertex builds H exactly once) and
+// then walks its work items: for a positive item v the whole N+(v), for a
+// negative item x the part of N+(x) after p; every walked w found in H closes
+// the triangle (p,v,w) or (x,p,w) (Algorithm 3, output steps).
+//
+// GB300 mapping: pivots are binned by deg+(p).
+//   BIN_WARP  deg+ <= warp_max: one warp per pivot, H = open-addressing hash
+//             table in the warp's slice of shared memory
+//   BIN_CTA   deg+ <= cta_max: one CTA per pivot, H in shared memory, the
+//             CTA's warps split the pivot's items
+//   BIN_HUB   larger: H = a global bitmap of n bits (L2 resident), several
+//             hubs at a time, all CTAs split the hubs' items
+// Inside a warp the items of a chunk (32 items) are flattened: lanes walk
+// consecutive positions of the concatenated walk ranges (coalesced loads),
+// find their item by a 5-step shuffle search over the exclusive prefix of
+// walk lengths, probe H, and count with __ballot_sync/__popc.
+// Work is handed out by per-bin atomic queues (persistent grids).
+#include "aot_internal.cuh"
+
+namespace aot {
+
+enum Mode { M_COUNT = 0, M_VERTEX = 1, M_LIST_COUNT = 2, M_LIST_WRITE = 3 };
+enum Queue { Q_WARP = 1, Q_CTA = 2, Q_HUB = 3 };
+
+struct KParams {
+  const uint32_t* off;
+  const uint32_t* adj;
+  const uint32_t* wofs;
+  const uint2* witem;
+  const uint32_t* wvert;
+  const uint32_t* wedge;
+  const uint32_t* pivots;  // this bin's pivots
+  uint32_t num_pivots;
+  uint64_t* tv;            // per-vertex counts (rank space)
+  uint32_t* tcnt;          // triangles per oriented edge
+  const uint64_t* toff;    // exclusive offsets per oriented edge
+  const int32_t* perm;
+  int32_t* out;
+  uint64_t cursor, cap;    // listing window [cursor, cursor + cap)
+  DevScalars* dev;
+};
+
+constexpr int MAX_HUBS = 64;
+struct HubGroup {
+  int count;
+  uint32_t words;                 // bitmap words per hub
+  uint32_t* bitmap;
+  uint32_t pivot[MAX_HUBS];
+  uint32_t ib[MAX_HUBS];          // first item
+  uint32_t ie[MAX_HUBS];          // end item
+  uint32_t cbeg[MAX_HUBS + 1];    // prefix of 32-item chunks
+};
+
+__device__ __forceinline__ unsigned range_mask(int lo, int hi) {  // bits [lo, hi)
+  unsigned a = lo >= 32 ? 0u : (lo <= 0 ? ~0u : (~0u << lo));
+  unsigned b = hi >= 32 ? ~0u : (hi <= 0 ? 0u : ((1u << hi) - 1u));
+  return a & b;
+}
+
+__device__ __forceinline__ int clamp_lane(int64_t x) {
+  return x < -1 ? -1 : (x > 64 ? 64 : (int)x);
+}
+
+// One warp walks items [c, min(c+32, ie)) of pivot p.  probe(w, slot) tests
+// H; on_w(w, slot) is called by every hitting lane (per-vertex counts of w).
+// Returns this lane's number of hits.
+template <int MODE, class Probe, class OnW>
+__device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uint32_t c,
+                                               uint32_t ie, Probe probe, OnW on_w) {
+  const unsigned lane = lane_id();
+  const uint32_t it = c + lane;
+  const bool has = it < ie;
+  uint2 r = has ? P.witem[it] : make_uint2(0u, 0u);
+  uint32_t vert = 0, edge = 0;
+  uint64_t tbase = 0;
+  if (MODE != M_COUNT && has) vert = P.wvert[it];
+  if (MODE >= M_LIST_COUNT && has) edge = P.wedge[it];
+  if (MODE == M_LIST_WRITE && has) {
+    uint64_t a = P.toff[edge], b = P.toff[edge + 1];
+    if (a == b || b <= P.cursor || a >= P.cursor + P.cap) r.y = r.x;  // nothing in the window
+    tbase = a;
+  }
+  const uint32_t len = r.y - r.x;
+  const uint32_t incl = warp_inclusive_scan(len);
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  const uint32_t excl = incl - len;
+  uint32_t ihits = 0;  // hits of the item held by this lane
+  uint32_t my = 0;     // hits found by this lane
+  for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    const bool act = q < total;
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      uint32_t e = __shfl_sync(FULL, excl, j + step);
+      if (e <= q) j += step;
+    }
+    const uint32_t jx = __shfl_sync(FULL, r.x, j);
+    const uint32_t je = __shfl_sync(FULL, excl, j);
+    uint32_t w = 0, slot = 0;
+    bool hit = false;
+    if (act) {
+      w = __ldg(P.adj + jx + (q - je));
+      hit = probe(w, slot);
+    }
+    const unsigned hm = __ballot_sync(FULL, hit);
+    if (MODE == M_LIST_WRITE) {
+      const uint32_t prev = __shfl_sync(FULL, ihits, j);
+      const unsigned peers = __match_any_sync(FULL, j);
+      const uint32_t tb_lo = __shfl_sync(FULL, (uint32_t)tbase, j);
+      const uint32_t tb_hi = __shfl_sync(FULL, (uint32_t)(tbase >> 32), j);
+      const uint32_t vj = __shfl_sync(FULL, vert, j);
+      if (hit) {
+        uint64_t idx = (((uint64_t)tb_hi << 32) | tb_lo) + prev +
+                       (uint32_t)__popc(hm & peers & lanemask_lt());
+        if (idx >= P.cursor && idx < P.cursor + P.cap) {
+          int32_t* o = P.out + 3 * (idx - P.cursor);
+          o[0] = P.perm[p < vj ? p : vj];
+          o[1] = P.perm[p < vj ? vj : p];
+          o[2] = P.perm[w];
+        }
+      }
+    }
+    if (MODE != M_COUNT) {
+      const int64_t lo = (int64_t)excl - (int64_t)q0, hi = (int64_t)incl - (int64_t)q0;
+      ihits += (uint32_t)__popc(hm & range_mask(clamp_lane(lo), clamp_lane(hi)));
+    }
+    if (hit) {
+      ++my;
+      if (MODE == M_VERTEX) on_w(w, slot);
+    }
+  }
+  if (MODE == M_VERTEX && has && ihits) atomicAdd((unsigned long long*)&P.tv[vert], (unsigned long long)ihits);
+  if (MODE == M_LIST_COUNT && has) P.tcnt[edge] = ihits;
+  return my;
+}
+
+// ------------------------------------------------------------ warp kernel
+constexpr int WARP_TS = 128;  // slots per warp table (deg+ <= 64)
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
+  __shared__ uint32_t sm[256 / 32][2 * WARP_TS];
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
+  uint32_t* tab = sm[wid];
+  uint32_t* cnt = sm[wid] + WARP_TS;
+  uint64_t found = 0;
+  while (true) {
+    uint32_t idx = 0;
+    if (lane == 0) idx = atomicAdd(&P.dev->counters[Q_WARP], 1u);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= P.num_pivots) break;
+    const uint32_t p = P.pivots[idx];
+    const uint32_t b = P.off[p], d = P.off[p + 1] - b;
+    uint32_t ts = 32;
+    while (ts < 2 * d) ts <<= 1;
+    const uint32_t mask = ts - 1;
+    for (uint32_t i = lane; i < ts; i += 32) {
+      tab[i] = EMPTY;
+      if (MODE == M_VERTEX) cnt[i] = 0;
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < d; i += 32) {
+      uint32_t w = P.adj[b + i], s = hash_slot(w, mask);
+      while (atomicCAS(&tab[s], EMPTY, w) != EMPTY) s = (s + 1) & mask;
+    }
+    __syncwarp();
+    auto probe = [&](uint32_t w, uint32_t& slot) -> bool {
+      uint32_t s = hash_slot(w, mask);
+      while (true) {
+        uint32_t k = tab[s];
+        if (k == w) { slot = s; return true; }
+        if (k == EMPTY) return false;
+        s = (s + 1) & mask;
+      }
+    };
+    auto on_w = [&](uint32_t, uint32_t slot) { atomicAdd(&cnt[slot], 1u); };
+    const uint32_t ib = P.wofs[p], ie = P.wofs[p + 1];
+    uint32_t ph = 0;
+    for (uint32_t c = ib; c < ie; c += 32) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w);
+    if (MODE == M_VERTEX) {
+      __syncwarp();
+      for (uint32_t i = lane; i < ts; i += 32)
+        if (cnt[i]) atomicAdd((unsigned long long*)&P.tv[tab[i]], (unsigned long long)cnt[i]);
+      uint32_t tot = warp_sum(ph);
+      if (lane == 0 && tot) atomicAdd((unsigned long long*)&P.tv[p], (unsigned long long)tot);
+    }
+    found += ph;
+    __syncwarp();
+  }
+  found = warp_sum(found);
+  if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
+}
+
+// ------------------------------------------------------------- CTA kernel
+template <int MODE>
+__global__ void __launch_bounds__(512) k_cta_pivots(KParams P, uint32_t ts_max) {
+  extern __shared__ uint32_t cta_sm[];
+  uint32_t* tab = cta_sm;
+  uint32_t* cnt = cta_sm + ts_max;
+  __shared__ uint32_t s_idx;
+  __shared__ unsigned long long s_hits;
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint64_t found = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_idx = atomicAdd(&P.dev->counters[Q_CTA], 1u);
+      s_hits = 0;
+    }
+    __syncthreads();
+    const uint32_t idx = s_idx;
+    if (idx >= P.num_pivots) break;
+    const uint32_t p = P.pivots[idx];
+    const uint32_t b = P.off[p], d = P.off[p + 1] - b;
+    uint32_t ts = 64;
+    while (ts < 2 * d) ts <<= 1;
+    const uint32_t mask = ts - 1;
+    for (uint32_t i = threadIdx.x; i < ts; i += blockDim.x) {
+      tab[i] = EMPTY;
+      if (MODE == M_VERTEX) cnt[i] = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+      uint32_t w = P.adj[b + i], s = hash_slot(w, mask);
+      while (atomicCAS(&tab[s], EMPTY, w) != EMPTY) s = (s + 1) & mask;
+    }
+    __syncthreads();
+    auto probe = [&](uint32_t w, uint32_t& slot) -> bool {
+      uint32_t s = hash_slot(w, mask);
+      while (true) {
+        uint32_t k = tab[s];
+        if (k == w) { slot = s; return true; }
+        if (k == EMPTY) return false;
+        s = (s + 1) & mask;
+      }
+    };
+    auto on_w = [&](uint32_t, uint32_t slot) { atomicAdd(&cnt[slot], 1u); };
+    const uint32_t ib = P.wofs[p], ie = P.wofs[p + 1];
+    uint32_t ph = 0;
+    for (uint32_t c = ib + 32 * wid; c < ie; c += 32 * nw) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w);
+    found += ph;
+    if (MODE == M_VERTEX) {
+      uint32_t tot = warp_sum(ph);
+      if (lane == 0 && tot) atomicAdd(&s_hits, (unsigned long long)tot);
+    }
+    __syncthreads();
+    if (MODE == M_VERTEX) {
+      for (uint32_t i = threadIdx.x; i < ts; i += blockDim.x)
+        if (cnt[i]) atomicAdd((unsigned long long*)&P.tv[tab[i]], (unsigned long long)cnt[i]);
+      if (threadIdx.x == 0 && s_hits) atomicAdd((unsigned long long*)&P.tv[p], s_hits);
+    }
+    __syncthreads();
+  }
+  found = warp_sum(found);
+  if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
+}
+
+// ------------------------------------------------------------- hub kernels
+__global__ void k_hub_bits(HubGroup G, const uint32_t* __restrict__ off,
+                           const uint32_t* __restrict__ adj, bool set) {
+  const int b = blockIdx.y;
+  const uint32_t p = G.pivot[b];
+  const uint32_t beg = off[p], end = off[p + 1];
+  uint32_t* bm = G.bitmap + (size_t)b * G.words;
+  for (uint32_t i = beg + blockIdx.x * blockDim.x + threadIdx.x; i < end; i += gridDim.x * blockDim.x) {
+    uint32_t w = adj[i];
+    if (set) atomicOr(&bm[w >> 5], 1u << (w & 31));
+    else bm[w >> 5] = 0u;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
+  const unsigned lane = lane_id();
+  const uint32_t nchunks = G.cbeg[G.count];
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint64_t found = 0;
+  for (uint32_t ch = gw; ch < nchunks; ch += nwarps) {
+    int b = 0;
+    while (b + 1 < G.count && G.cbeg[b + 1] <= ch) ++b;
+    const uint32_t p = G.pivot[b];
+    const uint32_t* bm = G.bitmap + (size_t)b * G.words;
+    const uint32_t c = G.ib[b] + 32 * (ch - G.cbeg[b]);
+    auto probe = [&](uint32_t w, uint32_t&) -> bool { return (__ldcg(bm + (w >> 5)) >> (w & 31)) & 1u; };
+    auto on_w = [&](uint32_t w, uint32_t) { atomicAdd((unsigned long long*)&P.tv[w], 1ull); };
+    uint32_t ph = walk_chunk<MODE>(P, p, c, G.ie[b], probe, on_w);
+    found += ph;
+    if (MODE == M_VERTEX) {
+      uint32_t tot = warp_sum(ph);
+      if (lane == 0 && tot) atomicAdd((unsigned long long*)&P.tv[p], (unsigned long long)tot);
+    }
+  }
+  found = warp_sum(found);
+  if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
+}
+
+__global__ void k_hub_info(const uint32_t* __restrict__ pivots, uint32_t nh,
+                           const uint32_t* __restrict__ wofs, const uint32_t* __restrict__ off,
+                           uint32_t* __restrict__ info) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nh) return;
+  uint32_t p = pivots[i];
+  info[4 * (size_t)i + 0] = p;
+  info[4 * (size_t)i + 1] = wofs[p];
+  info[4 * (size_t)i + 2] = wofs[p + 1];
+  info[4 * (size_t)i + 3] = off[p + 1] - off[p];
+}
+
+// ------------------------------------------------------------------ driver
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <int MODE>
+static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
+  const uint32_t nw = g->bin_count[BIN_WARP], nc = g->bin_count[BIN_CTA], nh = g->bin_count[BIN_HUB];
+  const int sms = sm_count();
+  if (nw) {
+    P.pivots = g->bin_pivots;
+    P.num_pivots = nw;
+    int per_sm = 0;
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_pivots<MODE>, 256, 0));
+    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    int64_t need = (nw + 7) / 8;
+    if (grid > need) grid = need;
+    k_warp_pivots<MODE><<<(unsigned)grid, 256, 0, s>>>(P);
+    AOT_TRY(last_launch());
+  }
+  if (nc) {
+    P.pivots = g->bin_pivots + nw;
+    P.num_pivots = nc;
+    uint32_t ts_max = 64;
+    while (ts_max < 2 * g->binned_cta_max) ts_max <<= 1;
+    size_t smem = (size_t)ts_max * 2 * sizeof(uint32_t);
+    static size_t attr_done[4] = {0, 0, 0, 0};
+    if (attr_done[MODE] < smem) {
+      AOT_CUDA(cudaFuncSetAttribute(k_cta_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_done[MODE] = smem;
+    }
+    const int threads = g->tune.cta_threads;
+    int per_sm = 0;
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cta_pivots<MODE>, threads, smem));
+    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > nc) grid = nc;
+    k_cta_pivots<MODE><<<(unsigned)grid, threads, smem, s>>>(P, ts_max);
+    AOT_TRY(last_launch());
+  }
+  if (nh) {
+    // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
+    const uint32_t* dp = g->bin_pivots + nw + nc;
+    k_hub_info<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->hubinfo);
+    AOT_TRY(last_launch());
+    uint32_t* hp = new uint32_t[4 * (size_t)nh];
+    AOT_CUDA(cudaMemcpyAsync(hp, g->hubinfo, sizeof(uint32_t) * 4 * nh, cudaMemcpyDeviceToHost, s));
+    AOT_CUDA(cudaStreamSynchronize(s));
+    const uint32_t words = (uint32_t)(((int64_t)g->n + 31) / 32);
+    int per_group = g->tune.hub_bitmaps < MAX_HUBS ? g->tune.hub_bitmaps : MAX_HUBS;
+    for (uint32_t h0 = 0; h0 < nh; h0 += per_group) {
+      HubGroup G;
+      G.count = (int)((nh - h0) < (uint32_t)per_group ? (nh - h0) : (uint32_t)per_group);
+      G.words = words;
+      G.bitmap = g->hub_bitmap;
+      G.cbeg[0] = 0;
+      uint32_t maxdeg = 0;
+      for (int b = 0; b < G.count; ++b) {
+        const uint32_t* h = hp + 4 * (size_t)(h0 + b);
+        G.pivot[b] = h[0];
+        G.ib[b] = h[1];
+        G.ie[b] = h[2];
+        G.cbeg[b + 1] = G.cbeg[b] + (h[2] - h[1] + 31) / 32;
+        if (h[3] > maxdeg) maxdeg = h[3];
+      }
+      dim3 sgrid((maxdeg + 255) / 256 < 64 ? (maxdeg + 255) / 256 : 64, G.count);
+      if (sgrid.x == 0) sgrid.x = 1;
+      k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, true);
+      AOT_TRY(last_launch());
+      int per_sm = 0;
+      AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hub_walk<MODE>, 256, 0));
+      int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+      int64_t need = ((int64_t)G.cbeg[G.count] + 7) / 8;
+      if (grid > need) grid = need;
+      if (grid < 1) grid = 1;
+      k_hub_walk<MODE><<<(unsigned)grid, 256, 0, s>>>(P, G);
+      AOT_TRY(last_launch());
+      k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, false);
+      AOT_TRY(last_launch());
+    }
+    delete[] hp;
+  }
+  return AOT_OK;
+}
+
+static KParams base_params(aot_graph* g) {
+  KParams P;
+  P.off = g->off;
+  P.adj = g->adj;
+  P.wofs = g->wofs;
+  P.witem = g->witem;
+  P.wvert = g->wvert;
+  P.wedge = g->wedge;
+  P.pivots = nullptr;
+  P.num_pivots = 0;
+  P.tv = g->tv;
+  P.tcnt = g->tcnt;
+  P.toff = g->toff;
+  P.perm = g->perm;
+  P.out = nullptr;
+  P.cursor = 0;
+  P.cap = 0;
+  P.dev = g->dev;
+  return P;
+}
+
+static aot_status reset_scalars(aot_graph* g, cudaStream_t s) {
+  AOT_CUDA(cudaMemsetAsync(&g->dev->total, 0, sizeof(unsigned long long), s));
+  AOT_CUDA(cudaMemsetAsync(g->dev->counters + 1, 0, sizeof(unsigned int) * 14, s));
+  return AOT_OK;
+}
+
+static aot_status check_route(aot_graph* g, aot_route route) {
+  if (!g) return AOT_ERR_INVALID_ARG;
+  if (route != AOT_ROUTE_PLAIN && route != AOT_ROUTE_PROBE) return AOT_ERR_NOT_READY;
+  if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
+  return AOT_OK;
+}
+
+__global__ void k_gather_counts(const uint64_t* __restrict__ tv, const int32_t* __restrict__ rank,
+                                int32_t n, uint64_t* __restrict__ out) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) out[v] = tv[rank[v]];
+}
+
+}  // namespace aot
+
+using namespace aot;
+
+extern "C" aot_status aot_count(aot_graph* g, aot_route route, uint64_t* h_total, aot_stream_t stream) {
+  AOT_TRY(check_route(g, route));
+  if (!h_total) return AOT_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  AOT_TRY(reset_scalars(g, s));
+  if (g->m > 0) AOT_TRY(launch_bins<M_COUNT>(g, base_params(g), s));
+  unsigned long long t = 0;
+  AOT_CUDA(cudaMemcpyAsync(&t, &g->dev->total, sizeof(t), cudaMemcpyDeviceToHost, s));
+  AOT_CUDA(cudaStreamSynchronize(s));
+  AOT_TRY(read_device_error(g, s));
+  *h_total = t;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_count_per_vertex(aot_graph* g, aot_route route, uint64_t* d_counts,
+                                           uint64_t* h_total, aot_stream_t stream) {
+  AOT_TRY(check_route(g, route));
+  if (!d_counts && g->n > 0) return AOT_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  AOT_TRY(reset_scalars(g, s));
+  if (g->n > 0) {
+    AOT_CUDA(cudaMemsetAsync(g->tv, 0, sizeof(uint64_t) * g->n, s));
+    if (g->m > 0) AOT_TRY(launch_bins<M_VERTEX>(g, base_params(g), s));
+    k_gather_counts<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(g->tv, g->rank, g->n, d_counts);
+    AOT_TRY(last_launch());
+  }
+  if (h_total) {
+    unsigned long long t = 0;
+    AOT_CUDA(cudaMemcpyAsync(&t, &g->dev->total, sizeof(t), cudaMemcpyDeviceToHost, s));
+    AOT_CUDA(cudaStreamSynchronize(s));
+    AOT_TRY(read_device_error(g, s));
+    *h_total = t;
+  }
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_out,
+                               uint64_t cap, uint64_t* h_written, uint64_t* h_next, aot_stream_t stream) {
+  AOT_TRY(check_route(g, route));
+  if (!h_written || !h_next || (cap > 0 && !d_out)) return AOT_ERR_INVALID_ARG;
+  if (!g->has_list) return AOT_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!g->list_ready) {
+    g->list_total = 0;
+    if (g->m > 0) {
+      AOT_TRY(reset_scalars(g, s));
+      AOT_CUDA(cudaMemsetAsync(g->tcnt, 0, sizeof(uint32_t) * g->m, s));
+      AOT_TRY(launch_bins<M_LIST_COUNT>(g, base_params(g), s));
+      AOT_TRY(scan_u32_u64(g->tcnt, g->toff, g->m, g->scan_tmp, s));
+      unsigned long long t = 0;
+      AOT_CUDA(cudaMemcpyAsync(&t, g->toff + g->m, sizeof(t), cudaMemcpyDeviceToHost, s));
+      AOT_CUDA(cudaStreamSynchronize(s));
+      AOT_TRY(read_device_error(g, s));
+      g->list_total = t;
+    }
+    g->list_ready = true;
+  }
+  const uint64_t T = g->list_total;
+  if (cursor > T) return AOT_ERR_INVALID_ARG;
+  uint64_t k = T - cursor < cap ? T - cursor : cap;
+  if (k > 0) {
+    KParams P = base_params(g);
+    P.out = d_out;
+    P.cursor = cursor;
+    P.cap = k;
+    AOT_TRY(reset_scalars(g, s));
+    AOT_TRY(launch_bins<M_LIST_WRITE>(g, P, s));
+    AOT_CUDA(cudaStreamSynchronize(s));
+    AOT_TRY(read_device_error(g, s));
+  }
+  *h_written = k;
+  *h_next = cursor + k;
+  return AOT_OK;
+}

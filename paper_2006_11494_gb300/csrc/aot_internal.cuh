@@ -1,0 +1,163 @@
+// aot_internal.cuh - internal declarations shared by the libaot translation
+// units: status plumbing, workspace carving, warp helpers, the graph handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/aot.h"
+
+namespace aot {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t EMPTY = 0xffffffffu;  // empty hash slot (no vertex has this rank)
+
+// Device error word bits (or-ed by kernels, read back by the API).
+constexpr uint32_t DEVERR_RANGE = 1u;    // input id outside [0, n)
+constexpr uint32_t DEVERR_CHECK = 2u;    // internal consistency check failed
+constexpr uint32_t DEVERR_TIMEOUT = 4u;  // a bounded wait ran out
+
+#define AOT_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return AOT_ERR_CUDA;         \
+  } while (0)
+#define AOT_TRY(call)                                   \
+  do {                                                  \
+    aot_status s_ = (call);                             \
+    if (s_ != AOT_OK) return s_;                        \
+  } while (0)
+
+inline aot_status last_launch() {
+  return cudaGetLastError() == cudaSuccess ? AOT_OK : AOT_ERR_CUDA;
+}
+
+// Bump allocator over a caller-owned device workspace.  With base == nullptr
+// it only measures (used by the *_workspace_size queries).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t used() const { return (off + 255) & ~size_t(255); }
+};
+
+inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x (x >= 1)
+  int b = 0;
+  while ((uint64_t(1) << b) < x) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(FULL, v, d);
+    if ((int)lane_id() >= d) v += o;
+  }
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+  return v;
+}
+__device__ __forceinline__ uint32_t hash_slot(uint32_t w, uint32_t mask) {
+  return (w * 2654435761u) & mask;  // Fibonacci-style multiplicative hash
+}
+
+// ------------------------------------------------------------ scan / sort
+// Exclusive prefix sum: out[i] = sum in[0..i), out[N] = total.
+size_t scan_tmp_bytes(int64_t N);
+aot_status scan_u32_u32(const uint32_t* in, uint32_t* out, int64_t N, void* tmp, cudaStream_t s);
+aot_status scan_u32_u64(const uint32_t* in, uint64_t* out, int64_t N, void* tmp, cudaStream_t s);
+aot_status scan_u64_u64(const uint64_t* in, uint64_t* out, int64_t N, void* tmp, cudaStream_t s);
+
+// LSD radix sort on bits [0, bits) of the keys; stable.  Returns (via *out)
+// whichever of the two key buffers holds the result (and the values with it).
+size_t radix_tmp_bytes(int64_t N);
+aot_status radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, int64_t N, int bits, void* tmp,
+                          cudaStream_t s, uint64_t** out);
+aot_status radix_sort_u32_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
+                                uint32_t* vals_alt, int64_t N, int bits, void* tmp,
+                                cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out);
+
+// ------------------------------------------------------------ graph handle
+// Pivot bins of the intersection kernels (by deg+ of the pivot).
+enum Bin { BIN_WARP = 0, BIN_CTA = 1, BIN_HUB = 2, NUM_BINS = 3 };
+
+struct Tuning {
+  uint32_t warp_max_outdeg = 64;    // BIN_WARP: 1..warp_max (table 2*pow2 slots)
+  uint32_t cta_max_outdeg = 4096;   // BIN_CTA: ..cta_max (smem hash)
+  int cta_threads = 512;
+  int warp_cta_threads = 256;
+  int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)
+};
+
+struct DevScalars {  // small device-resident scalars
+  unsigned long long total;      // triangle total
+  unsigned long long aux[7];
+  unsigned int err;              // error word
+  unsigned int counters[15];     // work-queue cursors
+};
+
+}  // namespace aot
+
+struct aot_graph {
+  int32_t n = 0;
+  int64_t m = 0;
+  int64_t num_edges = 0;
+  uint32_t flags = 0;
+  int bits = 1;          // ceil(log2(n)), >= 1
+  uint64_t W = 0, S = 0;
+  int32_t max_outdeg = 0;
+  // rank-space arrays in the workspace
+  int32_t* perm = nullptr;   // n : eta position -> original id
+  int32_t* rank = nullptr;   // n : original id -> eta position
+  uint32_t* off = nullptr;   // n+1
+  uint32_t* adj = nullptr;   // m
+  uint32_t* outdeg = nullptr;  // n
+  uint32_t* wofs = nullptr;  // n+1 work-CSR offsets per pivot
+  uint2* witem = nullptr;    // m : walk range [x, y) in adj
+  uint32_t* wvert = nullptr; // m : the walked vertex (v or x)
+  uint32_t* wedge = nullptr; // m : oriented edge id of the item
+  uint32_t* items = nullptr; // n : items per pivot
+  uint64_t* walk = nullptr;  // n : walk length per pivot
+  uint32_t* bin_pivots = nullptr;  // n : pivots grouped by bin
+  uint32_t* bin_flag = nullptr;    // n : scratch for binning
+  uint32_t* bin_pos = nullptr;     // n+1
+  uint32_t* hub_bitmap = nullptr;  // hub_bitmaps * ceil(n/32)
+  uint32_t* hubinfo = nullptr;     // 4 * n : hub descriptors
+  uint64_t* tv = nullptr;          // n : per-vertex counts (rank space)
+  uint32_t* tcnt = nullptr;        // m : triangles per oriented edge (list)
+  uint64_t* toff = nullptr;        // m+1
+  void* scan_tmp = nullptr;
+  aot::DevScalars* dev = nullptr;
+  bool has_list = false;
+  bool list_ready = false;
+  uint64_t list_total = 0;
+  // bins (host copy of counts), valid for the thresholds in `binned_for`
+  uint32_t bin_count[aot::NUM_BINS] = {0, 0, 0};
+  uint32_t binned_warp_max = 0, binned_cta_max = 0;
+  aot::Tuning tune;
+};
+
+namespace aot {
+aot_status bin_pivots(aot_graph* g, cudaStream_t s);
+aot_status read_device_error(aot_graph* g, cudaStream_t s);
+}  // namespace aot

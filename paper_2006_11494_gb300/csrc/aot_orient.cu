@@ -1,0 +1,462 @@
+// aot_orient.cu - orientation of an undirected edge list into the oriented
+// out-CSR of Algorithm 3 (first step) and the per-pivot work items of its
+// adaptive orientation (Sec. 3.1-3.2).
+//
+//  cleanup   key = (min << b) | max per non-loop pair, radix sort, unique
+//            (the input is an undirected simple graph, Sec. 2.1)
+//  degree    deg(v) over unique edges (warp-aggregated atomics)
+//  eta       stable radix sort of ids by degree (non-increasing by default),
+//            so ties keep the smaller id first (footnote of Sec. 3.2)
+//  orient    relabel to eta rank, key = (min rank << b) | max rank, radix
+//            sort: out-lists come out sorted by eta (the local order, Sec. 3.2)
+//  items     edge <u,v>: positive item of pivot u walking N+(v) if
+//            key(v) < key(u), else negative item of pivot v walking the part
+//            of N+(u) after v; key = (deg+, rank)
+//  bins      pivots with items, grouped by deg+ for the intersection kernels
+#include "aot_internal.cuh"
+
+namespace aot {
+
+constexpr uint64_t INVALID_KEY = ~0ull;
+
+__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            int64_t E, int32_t n, int bits, uint64_t* __restrict__ keys,
+                            DevScalars* dev) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  int32_t a = src[i], b = dst[i];
+  uint64_t k = INVALID_KEY;
+  if (a < 0 || a >= n || b < 0 || b >= n) {
+    atomicOr(&dev->err, DEVERR_RANGE);
+  } else if (a != b) {
+    uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+    k = ((uint64_t)lo << bits) | hi;
+  }
+  keys[i] = k;
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t E,
+                               uint32_t* __restrict__ flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  uint64_t k = keys[i];
+  flags[i] = (k != INVALID_KEY && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+// warp-aggregated atomicAdd of 1 to cnt[key]
+__device__ __forceinline__ void agg_inc(uint32_t* cnt, uint32_t key, bool active) {
+  unsigned grp = __match_any_sync(FULL, active ? key : 0xffffffffu);
+  if (active && lane_id() == (unsigned)(__ffs(grp) - 1)) atomicAdd(&cnt[key], (uint32_t)__popc(grp));
+}
+
+__global__ void k_compact_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ flags,
+                                 const uint32_t* __restrict__ pos, int64_t E, int bits,
+                                 uint64_t* __restrict__ ukeys, uint32_t* __restrict__ deg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = i < E && flags[i];
+  uint64_t k = act ? keys[i] : 0;
+  if (act) ukeys[pos[i]] = k;
+  uint32_t lo = (uint32_t)(k >> bits), hi = (uint32_t)(k & ((1ull << bits) - 1));
+  agg_inc(deg, lo, act);
+  agg_inc(deg, hi, act);
+}
+
+__global__ void k_eta_keys(const uint32_t* __restrict__ deg, int32_t n, int bits, bool desc,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  uint32_t d = deg[v];
+  keys[v] = desc ? (uint32_t)(((1ull << bits) - 1) - d) : d;
+  ids[v] = (uint32_t)v;
+}
+
+__global__ void k_rank_from_perm(const uint32_t* __restrict__ perm_sorted, int32_t n,
+                                 int32_t* __restrict__ perm, int32_t* __restrict__ rank) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  uint32_t v = perm_sorted[r];
+  perm[r] = (int32_t)v;
+  rank[v] = (int32_t)r;
+}
+
+__global__ void k_relabel(const uint64_t* __restrict__ ukeys, int64_t m, int bits,
+                          const int32_t* __restrict__ rank, uint64_t* __restrict__ okeys) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint64_t k = ukeys[i];
+  uint32_t a = (uint32_t)rank[(uint32_t)(k >> bits)];
+  uint32_t b = (uint32_t)rank[(uint32_t)(k & ((1ull << bits) - 1))];
+  uint32_t lo = min(a, b), hi = max(a, b);
+  okeys[i] = ((uint64_t)lo << bits) | hi;
+}
+
+__global__ void k_split_csr(const uint64_t* __restrict__ okeys, int64_t m, int bits,
+                            uint32_t* __restrict__ adj, uint32_t* __restrict__ esrc,
+                            uint32_t* __restrict__ outdeg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = i < m;
+  uint64_t k = act ? okeys[i] : 0;
+  uint32_t u = (uint32_t)(k >> bits);
+  if (act) {
+    adj[i] = (uint32_t)(k & ((1ull << bits) - 1));
+    esrc[i] = u;
+  }
+  agg_inc(outdeg, u, act);
+}
+
+__global__ void k_max_outdeg(const uint32_t* __restrict__ outdeg, int32_t n, DevScalars* dev) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t d = v < n ? outdeg[v] : 0u;
+  d = __reduce_max_sync(FULL, d);
+  if (lane_id() == 0 && d) atomicMax(&dev->counters[0], d);
+}
+
+__device__ __forceinline__ bool key_less(uint32_t dx, uint32_t x, uint32_t dy, uint32_t y) {
+  return dx < dy || (dx == dy && x < y);
+}
+
+// pivot of oriented edge e = <u,v> and its walk range
+__device__ __forceinline__ void edge_item(int64_t e, const uint32_t* __restrict__ esrc,
+                                          const uint32_t* __restrict__ adj,
+                                          const uint32_t* __restrict__ off,
+                                          const uint32_t* __restrict__ outdeg, uint32_t& pivot,
+                                          uint32_t& vert, uint2& range) {
+  uint32_t u = esrc[e], v = adj[e];
+  uint32_t du = outdeg[u], dv = outdeg[v];
+  if (key_less(dv, v, du, u)) {  // positive edge: pivot u walks N+(v)
+    pivot = u;
+    vert = v;
+    range = make_uint2(off[v], off[v] + dv);
+  } else {  // negative edge: pivot v walks N+(u) after v
+    pivot = v;
+    vert = u;
+    range = make_uint2((uint32_t)e + 1, off[u] + du);
+  }
+}
+
+__global__ void k_item_count(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
+                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
+                             int64_t m, uint32_t* __restrict__ items) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = e < m;
+  uint32_t p = 0, x;
+  uint2 r;
+  if (act) edge_item(e, esrc, adj, off, outdeg, p, x, r);
+  agg_inc(items, p, act);
+}
+
+__global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
+                            const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
+                            int64_t m, const uint32_t* __restrict__ wofs,
+                            uint32_t* __restrict__ cursor, uint2* __restrict__ witem,
+                            uint32_t* __restrict__ wvert, uint32_t* __restrict__ wedge) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = e < m;
+  uint32_t p = 0, x = 0;
+  uint2 r = make_uint2(0, 0);
+  if (act) edge_item(e, esrc, adj, off, outdeg, p, x, r);
+  unsigned grp = __match_any_sync(FULL, act ? p : 0xffffffffu);
+  unsigned leader = (unsigned)(__ffs(grp) - 1);
+  uint32_t base = 0;
+  if (act && lane_id() == leader) base = atomicAdd(&cursor[p], (uint32_t)__popc(grp));
+  base = __shfl_sync(FULL, base, leader);
+  if (act) {
+    uint32_t slot = wofs[p] + base + (uint32_t)__popc(grp & lanemask_lt());
+    witem[slot] = r;
+    wvert[slot] = x;
+    wedge[slot] = (uint32_t)e;
+  }
+}
+
+// warp per pivot: summed walk length; totals W and S
+__global__ void k_pivot_walk(const uint32_t* __restrict__ wofs, const uint2* __restrict__ witem,
+                             const uint32_t* __restrict__ outdeg, int32_t n,
+                             uint64_t* __restrict__ walk, DevScalars* dev) {
+  int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= n) return;
+  uint32_t b = wofs[p], e = wofs[p + 1];
+  uint64_t s = 0;
+  for (uint32_t i = b + lane_id(); i < e; i += 32) {
+    uint2 r = witem[i];
+    s += r.y - r.x;
+  }
+  s = warp_sum(s);
+  if (lane_id() == 0) {
+    walk[p] = s;
+    if (s) atomicAdd(&dev->total, (unsigned long long)s);
+    if (e > b) atomicAdd(&dev->aux[0], (unsigned long long)outdeg[p]);
+  }
+}
+
+// --------------------------------------------------------------------- bins
+__global__ void k_bin_flags(const uint32_t* __restrict__ items, const uint32_t* __restrict__ outdeg,
+                            int32_t n, uint32_t warp_max, uint32_t cta_max, int bin,
+                            uint32_t* __restrict__ flag) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t d = outdeg[p];
+  int b = d <= warp_max ? BIN_WARP : (d <= cta_max ? BIN_CTA : BIN_HUB);
+  flag[p] = (items[p] > 0 && b == bin) ? 1u : 0u;
+}
+
+__global__ void k_bin_scatter(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                              int32_t n, uint32_t base, uint32_t* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (flag[p]) out[base + pos[p]] = (uint32_t)p;
+}
+
+static inline unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+aot_status bin_pivots(aot_graph* g, cudaStream_t s) {
+  const int T = 256;
+  uint32_t base = 0;
+  for (int b = 0; b < NUM_BINS; ++b) {
+    uint32_t cnt = 0;
+    if (g->n > 0) {
+      k_bin_flags<<<grid_for(g->n, T), T, 0, s>>>(g->items, g->outdeg, g->n,
+                                                  g->tune.warp_max_outdeg,
+                                                  g->tune.cta_max_outdeg, b, g->bin_flag);
+      AOT_TRY(last_launch());
+      AOT_TRY(scan_u32_u32(g->bin_flag, g->bin_pos, g->n, g->scan_tmp, s));
+      k_bin_scatter<<<grid_for(g->n, T), T, 0, s>>>(g->bin_flag, g->bin_pos, g->n, base,
+                                                    g->bin_pivots);
+      AOT_TRY(last_launch());
+      AOT_CUDA(cudaMemcpyAsync(&cnt, g->bin_pos + g->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      AOT_CUDA(cudaStreamSynchronize(s));
+    }
+    g->bin_count[b] = cnt;
+    base += cnt;
+  }
+  g->binned_warp_max = g->tune.warp_max_outdeg;
+  g->binned_cta_max = g->tune.cta_max_outdeg;
+  return AOT_OK;
+}
+
+aot_status read_device_error(aot_graph* g, cudaStream_t s) {
+  uint32_t err = 0;
+  AOT_CUDA(cudaMemcpyAsync(&err, &g->dev->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AOT_CUDA(cudaStreamSynchronize(s));
+  if (err & DEVERR_RANGE) return AOT_ERR_VERTEX_RANGE;
+  if (err & DEVERR_TIMEOUT) return AOT_ERR_TIMEOUT;
+  if (err & DEVERR_CHECK) return AOT_ERR_DEVICE_CHECK;
+  return AOT_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+struct OrientLayout {
+  DevScalars* dev;
+  uint64_t* keysA;
+  uint64_t* keysB;
+  uint32_t* flags;
+  uint32_t* pos;
+  uint32_t* deg;
+  uint32_t* ek0; uint32_t* ek1; uint32_t* ev0; uint32_t* ev1;
+  int32_t* perm; int32_t* rank;
+  uint32_t* off; uint32_t* adj; uint32_t* outdeg;
+  uint32_t* wofs; uint32_t* items; uint64_t* walk;
+  uint32_t* bin_pivots; uint32_t* bin_flag; uint32_t* bin_pos;
+  uint32_t* hub_bitmap;
+  uint32_t* hubinfo;
+  uint64_t* tv;
+  uint32_t* tcnt; uint64_t* toff;
+  void* tmp;
+  size_t bytes;
+};
+
+static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flags, const Tuning& t) {
+  OrientLayout L;
+  Carve c(base);
+  int64_t Es = E > 0 ? E : 1;
+  int64_t ns = n > 0 ? n : 1;
+  L.dev = c.take<DevScalars>(1);
+  L.keysA = c.take<uint64_t>(Es);
+  L.keysB = c.take<uint64_t>(Es);
+  L.flags = c.take<uint32_t>(Es + 1);
+  L.pos = c.take<uint32_t>(Es + 1);
+  L.deg = c.take<uint32_t>(ns);
+  L.ek0 = c.take<uint32_t>(ns); L.ek1 = c.take<uint32_t>(ns);
+  L.ev0 = c.take<uint32_t>(ns); L.ev1 = c.take<uint32_t>(ns);
+  L.perm = c.take<int32_t>(ns); L.rank = c.take<int32_t>(ns);
+  L.off = c.take<uint32_t>(ns + 1);
+  L.adj = c.take<uint32_t>(Es);
+  L.outdeg = c.take<uint32_t>(ns);
+  L.wofs = c.take<uint32_t>(ns + 1);
+  L.items = c.take<uint32_t>(ns);
+  L.walk = c.take<uint64_t>(ns);
+  L.bin_pivots = c.take<uint32_t>(ns);
+  L.bin_flag = c.take<uint32_t>(ns);
+  L.bin_pos = c.take<uint32_t>(ns + 1);
+  L.hub_bitmap = c.take<uint32_t>((size_t)t.hub_bitmaps * (size_t)((ns + 31) / 32));
+  L.hubinfo = c.take<uint32_t>(4 * (size_t)ns);
+  L.tv = c.take<uint64_t>(ns);
+  L.tcnt = nullptr;
+  L.toff = nullptr;
+  if (!(flags & AOT_FLAG_NO_LIST)) {
+    L.tcnt = c.take<uint32_t>(Es);
+    L.toff = c.take<uint64_t>(Es + 1);
+  }
+  int64_t big = Es > ns ? Es : ns;  // the eta sort and the pivot scans run over n
+  size_t tb = radix_tmp_bytes(big);
+  size_t sb = scan_tmp_bytes(big + 1);
+  L.tmp = c.take<char>(tb > sb ? tb : sb);
+  L.bytes = c.used();
+  return L;
+}
+
+}  // namespace aot
+
+using namespace aot;
+
+extern "C" aot_status aot_orient_workspace_size(int64_t num_edges, int32_t num_vertices,
+                                                uint32_t flags, size_t* bytes) {
+  if (!bytes || num_edges < 0 || num_vertices < 0) return AOT_ERR_INVALID_ARG;
+  if (flags & ~(AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST)) return AOT_ERR_INVALID_ARG;
+  if (num_edges >= (int64_t(1) << 40)) return AOT_ERR_OVERFLOW;
+  Tuning t;
+  *bytes = carve_orient(nullptr, num_edges, num_vertices, flags, t).bytes;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int64_t num_edges,
+                                 int32_t num_vertices, uint32_t flags, void* d_workspace,
+                                 size_t ws_bytes, aot_stream_t stream, aot_graph** out) {
+  if (!out) return AOT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (num_edges < 0 || num_vertices < 0) return AOT_ERR_INVALID_ARG;
+  if (num_edges > 0 && (!d_src || !d_dst)) return AOT_ERR_INVALID_ARG;
+  if (flags & ~(AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST)) return AOT_ERR_INVALID_ARG;
+  if (num_edges >= (int64_t(1) << 40)) return AOT_ERR_OVERFLOW;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) return AOT_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Tuning tune;
+  OrientLayout L = carve_orient(d_workspace, num_edges, num_vertices, flags, tune);
+  if (ws_bytes < L.bytes) return AOT_ERR_WORKSPACE;
+  if (num_edges > 0 && num_vertices == 0) return AOT_ERR_VERTEX_RANGE;
+
+  aot_graph* g = new aot_graph();
+  g->tune = tune;
+  g->n = num_vertices;
+  g->num_edges = num_edges;
+  g->flags = flags;
+  g->bits = num_vertices > 1 ? ceil_log2((uint64_t)num_vertices) : 1;
+  g->dev = L.dev;
+  g->perm = L.perm; g->rank = L.rank; g->off = L.off; g->outdeg = L.outdeg;
+  g->wofs = L.wofs; g->items = L.items; g->walk = L.walk;
+  g->bin_pivots = L.bin_pivots; g->bin_flag = L.bin_flag; g->bin_pos = L.bin_pos;
+  g->hub_bitmap = L.hub_bitmap; g->hubinfo = L.hubinfo; g->tv = L.tv;
+  g->tcnt = L.tcnt; g->toff = L.toff; g->has_list = !(flags & AOT_FLAG_NO_LIST);
+  g->scan_tmp = L.tmp;
+  g->adj = L.adj;
+  auto fail = [&](aot_status st) { delete g; return st; };
+
+  const int T = 256;
+  const int32_t n = num_vertices;
+  const int64_t E = num_edges;
+  const int bits = g->bits;
+  if (cudaMemsetAsync(L.dev, 0, sizeof(DevScalars), s) != cudaSuccess) return fail(AOT_ERR_CUDA);
+  if (n > 0) {
+    if (cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
+        cudaMemsetAsync(L.outdeg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
+        cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess)
+      return fail(AOT_ERR_CUDA);
+  }
+  // 1. cleanup: keys, sort, unique
+  int64_t m = 0;
+  uint64_t* sorted = L.keysA;
+  uint64_t* other = L.keysB;
+  if (E > 0) {
+    k_make_keys<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, L.dev);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    aot_status st = radix_sort_u64(L.keysA, L.keysB, E, 2 * bits, L.tmp, s, &sorted);
+    if (st) return fail(st);
+    other = sorted == L.keysA ? L.keysB : L.keysA;
+    k_unique_flags<<<grid_for(E, T), T, 0, s>>>(sorted, E, L.flags);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    st = scan_u32_u32(L.flags, L.pos, E, L.tmp, s);
+    if (st) return fail(st);
+    uint32_t mm = 0;
+    if (cudaMemcpyAsync(&mm, L.pos + E, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+      return fail(AOT_ERR_CUDA);
+    st = read_device_error(g, s);
+    if (st) return fail(st);
+    m = mm;
+    k_compact_unique<<<grid_for(E, T), T, 0, s>>>(sorted, L.flags, L.pos, E, bits, other, L.deg);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  g->m = m;
+  // 2. eta: stable sort of ids by degree key
+  if (n > 0) {
+    k_eta_keys<<<grid_for(n, T), T, 0, s>>>(L.deg, n, bits, !(flags & AOT_ETA_DEG_ASC), L.ek0,
+                                            L.ev0);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    uint32_t *ko, *vo;
+    aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, s, &ko, &vo);
+    if (st) return fail(st);
+    k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.perm, L.rank);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  // 3. orient: relabel, sort, split into out-CSR
+  uint32_t* esrc = L.flags;  // the cleanup flags are dead now
+  if (m > 0) {
+    uint64_t* ukeys = other;
+    uint64_t* okeys = sorted;  // reuse the other buffer
+    k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, okeys);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    uint64_t* osorted;
+    aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, s, &osorted);
+    if (st) return fail(st);
+    k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, L.adj, esrc, L.outdeg);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  if (n > 0) {
+    aot_status st = scan_u32_u32(L.outdeg, L.off, n, L.tmp, s);
+    if (st) return fail(st);
+    k_max_outdeg<<<grid_for(n, T), T, 0, s>>>(L.outdeg, n, L.dev);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  } else {
+    if (cudaMemsetAsync(L.off, 0, sizeof(uint32_t), s)) return fail(AOT_ERR_CUDA);
+  }
+  // 4. work items (they overwrite the dead key buffers)
+  g->witem = reinterpret_cast<uint2*>(L.keysA);
+  g->wvert = reinterpret_cast<uint32_t*>(L.keysB);
+  g->wedge = reinterpret_cast<uint32_t*>(L.keysB) + (E > 0 ? E : 1);
+  if (m > 0) {
+    k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  if (n > 0) {
+    aot_status st = scan_u32_u32(L.items, L.wofs, n, L.tmp, s);
+    if (st) return fail(st);
+    if (cudaMemsetAsync(L.bin_flag, 0, sizeof(uint32_t) * n, s)) return fail(AOT_ERR_CUDA);
+  } else {
+    if (cudaMemsetAsync(L.wofs, 0, sizeof(uint32_t), s)) return fail(AOT_ERR_CUDA);
+  }
+  if (m > 0) {
+    k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, L.bin_flag,
+                                             g->witem, g->wvert, g->wedge);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  if (n > 0) {
+    k_pivot_walk<<<grid_for((int64_t)n * 32, T), T, 0, s>>>(L.wofs, g->witem, L.outdeg, n, L.walk,
+                                                           L.dev);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  DevScalars hs;
+  if (cudaMemcpyAsync(&hs, L.dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, s) ||
+      cudaStreamSynchronize(s))
+    return fail(AOT_ERR_CUDA);
+  if (hs.err) return fail(hs.err & DEVERR_RANGE ? AOT_ERR_VERTEX_RANGE : AOT_ERR_DEVICE_CHECK);
+  g->W = hs.total;
+  g->S = hs.aux[0];
+  g->max_outdeg = (int32_t)hs.counters[0];
+  // 5. bins
+  aot_status st = bin_pivots(g, s);
+  if (st) return fail(st);
+  *out = g;
+  return AOT_OK;
+}

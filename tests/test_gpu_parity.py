@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by
+element, on seeded inputs (bit-exact: every output here is an integer)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import gpu_graph, to_dev, u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def check_full(n, s, d, flags=0, order=oracle.ORDER_DESC, listing=True, tuning=None, chunk=1 << 20):
+    import paper_2006_11494_gb300 as aot
+    ref = oracle.Graph(n, s, d)
+    g = gpu_graph(n, s, d, flags)
+    if tuning:
+        g.set_tuning(**tuning)
+    assert g.m == ref.m
+    T_ref, t_ref = ref.count_per_vertex()
+    assert g.count() == T_ref
+    T, t = g.count_per_vertex()
+    assert T == T_ref
+    assert np.array_equal(u64(t), t_ref)
+    if listing:
+        lst = g.list(chunk=chunk).cpu().numpy()
+        assert np.array_equal(lst, ref.list_canonical(order))
+    for r in (aot.ROUTE_PROBE,):
+        assert g.count(r) == T_ref
+    return g, ref
+
+
+# ------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("case", ["k3", "k4", "k10", "k70", "w4", "w50", "w300", "bip", "tri",
+                                  "f1", "f30", "c3", "c100", "star", "tree"])
+def test_closed_forms(case):
+    make = {
+        "k3": lambda: gg.complete(3), "k4": lambda: gg.complete(4), "k10": lambda: gg.complete(10),
+        "k70": lambda: gg.complete(70), "w4": lambda: gg.wheel(4), "w50": lambda: gg.wheel(50),
+        "w300": lambda: gg.wheel(300), "bip": lambda: gg.random_bipartite(40, 70, 0.3, 1),
+        "tri": lambda: gg.complete_multipartite(5, 6, 7), "f1": lambda: gg.friendship(1),
+        "f30": lambda: gg.friendship(30), "c3": lambda: gg.cycle(3), "c100": lambda: gg.cycle(100),
+        "star": lambda: gg.star(1000), "tree": lambda: gg.random_tree(500, 2),
+    }[case]
+    n, s, d = make()
+    check_full(n, s, d)
+
+
+# --------------------------------------------------------- config 1 (ER)
+def test_er_c1_full_parity_and_orientation():
+    n, s, d = gg.er_c1()
+    g, ref = check_full(n, s, d)
+    rank, perm, off, adj = ref.orient(oracle.ORDER_DESC)
+    ex = g.export()
+    assert np.array_equal(ex["perm"].cpu().numpy(), perm)
+    assert np.array_equal(ex["rank"].cpu().numpy(), rank)
+    assert np.array_equal(ex["out_off"].cpu().numpy().astype(np.int64), off)
+    assert np.array_equal(ex["out_adj"].cpu().numpy(), adj)
+    items, walk = ref.work(oracle.ORDER_DESC)
+    assert np.array_equal(ex["items"].cpu().numpy().astype(np.uint32), items)
+    assert np.array_equal(ex["walk"].cpu().numpy().astype(np.uint64), walk)
+    c = ref.costs(oracle.ORDER_DESC)
+    assert g.info["W"] == c["walk"]
+    outd = np.diff(off)
+    assert g.info["S"] == int(outd[items > 0].sum())
+    assert g.info["max_outdeg"] == int(outd.max())
+
+
+# ------------------------------------------------------- R-MAT, small scales
+@pytest.mark.parametrize("scale,seed", [(8, 1), (10, 2), (12, 3), (14, 2)])
+def test_rmat_full_parity(scale, seed):
+    n, s, d = gg.rmat_cfg(scale, seed)
+    g, ref = check_full(n, s, d)
+    assert g.info["W"] == ref.costs()["walk"]
+
+
+def test_chunglu_full_parity():
+    s, d = gg.chunglu(1 << 13, 2.1, 24.0, seed=5)
+    check_full(1 << 13, s, d)
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_bitmaps=1),      # everything on the hub path
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_bitmaps=32),
+    dict(warp_max_outdeg=64, cta_max_outdeg=64),                   # warp + hub
+    dict(warp_max_outdeg=1, cta_max_outdeg=8192, cta_threads=128),  # almost all CTA
+    dict(warp_max_outdeg=16, cta_max_outdeg=256, cta_threads=1024, hub_bitmaps=3),
+])
+def test_every_bin_gives_the_same_answer(tuning):
+    n, s, d = gg.rmat_cfg(13, 7)
+    check_full(n, s, d, tuning=tuning)
+
+
+def test_asc_order_orientation_and_parity():
+    import paper_2006_11494_gb300 as aot
+    n, s, d = gg.rmat_cfg(12, 5)
+    g, ref = check_full(n, s, d, flags=aot.ETA_DEG_ASC, order=oracle.ORDER_ASC)
+    rank, perm, off, adj = ref.orient(oracle.ORDER_ASC)
+    ex = g.export()
+    assert np.array_equal(ex["perm"].cpu().numpy(), perm)
+    assert np.array_equal(ex["out_adj"].cpu().numpy(), adj)
+    assert g.info["W"] == ref.costs(oracle.ORDER_ASC)["walk"]
+
+
+def test_hub_wheel():
+    n, s, d = gg.wheel(20000)  # hub deg+ 20000: beyond the shared-memory bins
+    g, ref = check_full(n, s, d)
+    assert g.info["max_outdeg"] == 20000
+
+
+def test_complete_dense():
+    n, s, d = gg.complete(300)
+    check_full(n, s, d)
+
+
+# ------------------------------------------------------------- edge cases
+def test_empty_and_degenerate():
+    import paper_2006_11494_gb300 as aot
+    e = np.zeros(0, np.int32)
+    for n in (0, 1, 5):
+        g = gpu_graph(n, e, e)
+        assert g.m == 0 and g.count() == 0
+        T, t = g.count_per_vertex()
+        assert T == 0 and not u64(t).any()
+        assert g.list().shape == (0, 3)
+    # loops only
+    g = gpu_graph(4, np.array([1, 2, 2], np.int32), np.array([1, 2, 2], np.int32))
+    assert g.m == 0 and g.count() == 0
+    # single edge, single triangle with duplicates, reversals and loops
+    g = gpu_graph(3, np.array([0], np.int32), np.array([2], np.int32))
+    assert g.m == 1 and g.count() == 0
+    s = np.array([0, 1, 2, 1, 0, 2, 2], np.int32)
+    d = np.array([1, 2, 0, 0, 2, 1, 2], np.int32)
+    check_full(3, s, d)
+
+
+def test_duplicates_reversals_loops_invariance():
+    n, s, d = gg.rmat_cfg(11, 3)
+    g0, ref = check_full(n, s, d)
+    rng = np.random.default_rng(0)
+    loops = rng.integers(0, n, 500).astype(np.int32)
+    s2 = np.concatenate([d, s, loops, s[:1000]])
+    d2 = np.concatenate([s, d, loops, d[:1000]])
+    idx = rng.permutation(s2.size)
+    g1, _ = check_full(n, s2[idx], d2[idx])
+    assert g1.m == g0.m and g1.info["W"] == g0.info["W"]
+
+
+def test_invalid_ids_are_rejected():
+    import paper_2006_11494_gb300 as aot
+    for bad in ([0, 5], [-1, 2], [2, 2147483647]):
+        s = np.array([0, 1, bad[0]], np.int32)
+        d = np.array([1, 2, bad[1]], np.int32)
+        with pytest.raises(aot.AotError) as e:
+            gpu_graph(5, s, d)
+        assert e.value.status == aot.ERR_VERTEX_RANGE
+    # the context stays usable
+    n, s, d = gg.complete(5)
+    assert gpu_graph(n, s, d).count() == 10
+
+
+def test_relabel_invariance():
+    n, s, d = gg.rmat_cfg(12, 9)
+    g0 = gpu_graph(n, s, d)
+    perm = np.random.default_rng(3).permutation(n).astype(np.int32)
+    g1 = gpu_graph(n, perm[s], perm[d])
+    assert g0.count() == g1.count()
+    _, t0 = g0.count_per_vertex()
+    _, t1 = g1.count_per_vertex()
+    t0, t1 = u64(t0), u64(t1)
+    assert np.array_equal(t1[perm], t0)
+
+
+# ------------------------------------------------------------ listing chunks
+@pytest.mark.parametrize("cap", [1, 3, 1000, 4096])
+def test_chunked_listing(cap):
+    import torch
+    import paper_2006_11494_gb300 as aot
+    n, s, d = gg.rmat_cfg(10, 4)
+    ref = oracle.Graph(n, s, d).list_canonical()
+    g = gpu_graph(n, s, d)
+    out = torch.empty(3 * cap, dtype=torch.int32, device="cuda")
+    parts, cursor = [], 0
+    while True:
+        k, nxt = aot.aot_list(g.handle, aot.ROUTE_PLAIN, cursor, out, cap)
+        assert nxt == cursor + k
+        parts.append(out[: 3 * k].cpu().numpy().reshape(-1, 3))
+        cursor = nxt
+        if k < cap:
+            break
+    got = np.concatenate(parts)
+    assert np.array_equal(got, ref)
+    # resume from an arbitrary cursor
+    mid = len(ref) // 3
+    k, nxt = aot.aot_list(g.handle, aot.ROUTE_PLAIN, mid, out, cap)
+    assert np.array_equal(out[: 3 * k].cpu().numpy().reshape(-1, 3), ref[mid:mid + k])
+    k, nxt = aot.aot_list(g.handle, aot.ROUTE_PLAIN, len(ref), out, cap)
+    assert k == 0 and nxt == len(ref)
+    with pytest.raises(aot.AotError):
+        aot.aot_list(g.handle, aot.ROUTE_PLAIN, len(ref) + 1, out, cap)
+
+
+def test_no_list_workspace():
+    import torch
+    import paper_2006_11494_gb300 as aot
+    n, s, d = gg.rmat_cfg(9, 4)
+    g = gpu_graph(n, s, d, aot.FLAG_NO_LIST)
+    assert g.count() == oracle.Graph(n, s, d).count()
+    out = torch.empty(30, dtype=torch.int32, device="cuda")
+    with pytest.raises(aot.AotError) as e:
+        aot.aot_list(g.handle, aot.ROUTE_PLAIN, 0, out, 10)
+    assert e.value.status == aot.ERR_WORKSPACE
+
+
+def test_side_stream():
+    import torch
+    n, s, d = gg.rmat_cfg(11, 8)
+    T_ref = oracle.Graph(n, s, d).count()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        src, dst = to_dev(s, d)
+        import paper_2006_11494_gb300 as aot
+        g = aot.OrientedGraph(src, dst, n, 0, st)
+        assert g.count(stream=st) == T_ref
