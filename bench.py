@@ -1,0 +1,374 @@
+"""Benchmark of the AOT hot path on GB300.
+
+One step = the whole hot path over one synthetic graph resident in HBM:
+orientation (cleanup, eta, oriented CSR, work items, bins) followed by the
+per-vertex triangle count (walk + probe of Algorithm 3, every pivot's index
+built once).  Workload: R-MAT scale 24, edge factor 16, (a,b,c,d) =
+(.57,.19,.19,.05), ids permuted, seed 3 (synthetic stand-in for the paper's
+real graphs).  Metric: oriented edges per second (m / step time); the JSON
+line also carries triangles per second, the count-phase time, and the
+roofline of the dominant kernel measured with CUDA events inside the timed
+region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the slow reference program of this
+project) on a bounded prefix sample of the same edge stream.
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the graph does not shard in this build: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "oriented edges/s & triangles/s at R-MAT s24, learned vs plain; HBM roofline frac"
+UNIT = "oriented edges/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--route", default="plain", choices=["plain", "learned"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=23,
+                    help="log2 of the edge-stream prefix the CPU baseline runs on")
+    return ap.parse_args()
+
+
+# -------------------------------------------------------------- utilities
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "aot_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------- algorithmic bytes
+def bytes_per_kernel(info, bins, E, n):
+    """Algorithmic HBM bytes of one step, per kernel family."""
+    m, bits = info["m"], max(1, math.ceil(math.log2(max(n, 2))))
+    passes_keys = math.ceil(2 * bits / 8)
+    passes_eta = math.ceil(bits / 8)
+    out = {}
+    # radix sort: scatter reads and writes every key (and value) once per pass
+    out["k_radix_scatter"] = (passes_keys * (16 * E + 16 * m) + passes_eta * 16 * n,
+                              2 * passes_keys + passes_eta)
+    out["k_radix_hist"] = (passes_keys * (8 * E + 8 * m) + passes_eta * 4 * n,
+                           2 * passes_keys + passes_eta)
+
+    def walk_bytes(b):
+        st = bins[b]
+        # stage N+(p), read the pivot's offsets, the items' walk ranges and
+        # walked vertices, and every walked adjacency entry once
+        return 4 * st["staged"] + 16 * st["pivots"] + 12 * st["items"] + 4 * st["walk"]
+
+    out["k_warp_pivots/vertex"] = (walk_bytes("warp"), 1)
+    out["k_cta_pivots/vertex"] = (walk_bytes("cta"), 1)
+    out["k_hub_walk/vertex"] = (walk_bytes("hub") - 4 * bins["hub"]["staged"], None)
+    return out
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(a):
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_2006_11494_gb300 as aot
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n = 1 << a.scale
+    E = 16 << a.scale
+    h_src = torch.empty(E, dtype=torch.int32).pin_memory()
+    h_dst = torch.empty(E, dtype=torch.int32).pin_memory()
+    gg.rmat(a.scale, 16, a.seed, out=(h_src.numpy(), h_dst.numpy()))
+    src = h_src.to(dev)
+    dst = h_dst.to(dev)
+    ws_bytes = aot.aot_orient_workspace_size(E, n, aot.FLAG_NO_LIST)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    counts = torch.empty(n, dtype=torch.int64, device=dev)
+    h_counts = torch.empty(n, dtype=torch.int64).pin_memory()
+    route = aot.ROUTE_PLAIN if a.route == "plain" else aot.ROUTE_LEARNED
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s_src, s_dst):
+        h = aot.aot_orient(s_src, s_dst, n, aot.FLAG_NO_LIST, ws, stream)
+        aot.aot_count_per_vertex(h, route, counts, want_total=False, stream=stream)
+        return h
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (also the reference values of this run)
+    for _ in range(max(a.warmup, 3)):
+        h = step(src, dst)
+        info = aot.aot_graph_info(h)
+        bins = aot.aot_graph_bins(h)
+        aot.aot_graph_destroy(h)
+    torch.cuda.synchronize()
+    T = int(counts.sum().item()) // 3
+
+    # timed region: K steps, inputs resident in HBM (2 GB edge list > L2)
+    l0 = aot.aot_kernel_launches()
+    aot.aot_profile_begin()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            aot.aot_graph_destroy(step(src, dst))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    prof = aot.aot_profile_end()
+    launches = aot.aot_kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # count phase alone (plain route), for context
+    h = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST, ws, stream)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(stream)
+    for _ in range(a.steps):
+        aot.aot_count_per_vertex(h, route, counts, want_total=False, stream=stream)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    count_ms = c0.elapsed_time(c1) / a.steps
+    aot.aot_graph_destroy(h)
+
+    # end to end: pinned host edge list in, per-vertex counts out, every step
+    e2e = None
+    if not a.no_e2e:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d_src = torch.empty_like(src)
+        d_dst = torch.empty_like(dst)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(a.steps):
+            d_src.copy_(h_src, non_blocking=True)
+            d_dst.copy_(h_dst, non_blocking=True)
+            aot.aot_graph_destroy(step(d_src, d_dst))
+            h_counts.copy_(counts, non_blocking=True)
+            stream.synchronize()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / a.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * info["m"] / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n}
+        del d_src, d_dst
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peak()
+    bpk = bytes_per_kernel(info, bins, E, n)
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (nl, tot_ms) = dom
+        per_launch_ms = tot_ms / nl
+        b = bpk.get(name)
+        if b:
+            total_bytes, lpstep = b
+            lps = nl / a.steps
+            per_launch_bytes = total_bytes / lps
+            achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "launch_ms": per_launch_ms, "alg_bytes_per_launch": per_launch_bytes}
+        else:
+            roof = {"bound": "hbm", "kernel": name, "achieved": None, "peak": peak, "unit": "GB/s",
+                    "frac": None, "traffic": None}
+    total_prof = sum(v[1] for v in prof.values()) or 1.0
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total_prof, 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(a.scale, a.seed, a.cpu_sample_log2, h_src.numpy(), h_dst.numpy())
+
+    value = world * info["m"] / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "R-MAT scale %d edge factor 16 (a,b,c,d)=(.57,.19,.19,.05) seed %d, "
+                               "eta = degree non-increasing" % (a.scale, a.seed),
+                   "step": "aot_orient + aot_count_per_vertex (%s route)" % a.route,
+                   "n": n, "generated_edges": E, "m": info["m"], "W": info["W"], "S": info["S"],
+                   "max_outdeg": info["max_outdeg"], "triangles": T,
+                   "l2": "inputs larger than L2 (2 GB edge list, 129 MB L2)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "triangles_per_s": world * T / (ms / 1e3),
+        "count_phase": {"ms": count_ms, "oriented_edges_per_s": info["m"] / (count_ms / 1e3),
+                        "triangles_per_s": T / (count_ms / 1e3), "probes_per_s": info["W"] / (count_ms / 1e3)},
+        "bins": bins,
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_baseline(scale, seed, log2_sample, src_np, dst_np):
+    """The oracle, as it stands, on a prefix of the same edge stream."""
+    import oracle
+    n = 1 << scale
+    E = 1 << log2_sample
+    t0 = time.perf_counter()
+    g = oracle.Graph(n, src_np[:E], dst_np[:E])
+    T, _ = g.count_per_vertex()
+    dt = time.perf_counter() - t0
+    return {"value": g.m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first 2^%d of the %d generated pairs of the same R-MAT stream "
+                      "(m=%d, T=%d; far sparser in triangles than the full graph); cleanup + "
+                      "per-vertex count, %.1f s" % (log2_sample, 16 << scale, g.m, T, dt)}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import graphgen as gg
+    import oracle
+    log2_sample = 21
+    E = 1 << log2_sample
+    n = 1 << a.scale
+    # the first E pairs of the same stream (pairs are drawn independently)
+    src, dst = gg.rmat(a.scale, 16, a.seed, num_edges=E)
+
+    def step():
+        g = oracle.Graph(n, src, dst)
+        g.count_per_vertex()
+        return g.m
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        m = step()
+    dt = (time.perf_counter() - t0) / a.steps
+    v = m / dt
+    sample = "first 2^%d generated pairs of the R-MAT scale-%d stream (m=%d); cleanup + per-vertex count" % (
+        log2_sample, a.scale, m)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "R-MAT scale %d edge factor 16 seed %d (bounded prefix sample)" % (a.scale, a.seed)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

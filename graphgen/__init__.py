@@ -89,9 +89,11 @@ def er(n: int, num_edges: int, seed: int, out=None, threads: int = 0):
 
 
 def rmat(scale: int, edge_factor: int = 16, seed: int = 2, a=0.57, b=0.19, c=0.19,
-         permute: bool = True, out=None, threads: int = 0):
-    """R-MAT with 2^scale vertices and edge_factor * 2^scale generated pairs."""
-    num_edges = edge_factor << scale
+         permute: bool = True, out=None, threads: int = 0, num_edges: int = None):
+    """R-MAT with 2^scale vertices and edge_factor * 2^scale generated pairs
+    (or only the first ``num_edges`` pairs of that stream)."""
+    if num_edges is None:
+        num_edges = edge_factor << scale
     src, dst = _out(num_edges, out)
     rc = _L().gg_rmat(scale, num_edges, a, b, c, seed, int(permute), _ptr(src), _ptr(dst), threads)
     if rc:

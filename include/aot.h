@@ -156,6 +156,17 @@ typedef struct {
   int32_t hub_bitmaps;
 } aot_tuning;
 
+/* Work statistics of one pivot bin under the current tuning. */
+typedef struct {
+  uint64_t pivots; /* pivots with at least one item in this bin         */
+  uint64_t items;  /* their work items (oriented edges)                 */
+  uint64_t walk;   /* summed walk length of those items (part of W)     */
+  uint64_t staged; /* summed deg+ of those pivots (index entries built) */
+} aot_bin_stats;
+
+/* Statistics of the three bins (warp, CTA, hub), in that order. */
+aot_status aot_graph_bins(const aot_graph* g, aot_bin_stats out[3]);
+
 /* Current tuning of a graph (defaults after aot_orient). */
 aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t);
 
@@ -163,6 +174,27 @@ aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t);
  * return AOT_ERR_INVALID_ARG and leave the graph unchanged.  hub_bitmaps may
  * not exceed the value the workspace was sized for (32). */
 aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t s);
+
+/* ---- launch accounting and profiling (no effect on results) ---- */
+
+/* Number of kernels this library has launched in this process. */
+unsigned long long aot_kernel_launches(void);
+
+/* One profiled kernel: its name, launches and summed device time. */
+typedef struct {
+  char name[64];
+  uint64_t launches;
+  double total_ms;
+} aot_profile_entry;
+
+/* Start recording: every later launch is bracketed by a pair of CUDA events
+ * on its stream (a previous recording is discarded). */
+aot_status aot_profile_begin(void);
+
+/* Stop recording, wait for the recorded events, and aggregate by kernel name:
+ * up to cap entries are written to out, *count receives the number of
+ * distinct kernels. */
+aot_status aot_profile_end(aot_profile_entry* out, int32_t cap, int32_t* count);
 
 /* Free the host handle (the workspace stays with the caller). */
 aot_status aot_graph_destroy(aot_graph* g);

@@ -46,10 +46,20 @@ SIGNATURES = {
     "aot_count_per_vertex": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.POINTER(U64), P]),
     "aot_list": (ctypes.c_int, [P, ctypes.c_int, U64, P, U64, ctypes.POINTER(U64),
                                 ctypes.POINTER(U64), P]),
+    "aot_graph_bins": (ctypes.c_int, [P, P]),
     "aot_graph_get_tuning": (ctypes.c_int, [P, P]),
     "aot_graph_set_tuning": (ctypes.c_int, [P, P, P]),
     "aot_graph_destroy": (ctypes.c_int, [P]),
+    "aot_kernel_launches": (ctypes.c_ulonglong, []),
+    "aot_profile_begin": (ctypes.c_int, []),
+    "aot_profile_end": (ctypes.c_int, [P, I32, ctypes.POINTER(I32)]),
 }
+
+
+class ProfileEntry(ctypes.Structure):
+    """Mirror of aot_profile_entry."""
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -166,6 +176,17 @@ def aot_list(handle: int, route: int, cursor: int, out, cap: int, stream=None):
     return k.value, nxt.value
 
 
+BIN_NAMES = ("warp", "cta", "hub")
+
+
+def aot_graph_bins(handle: int) -> dict:
+    """{bin name: {pivots, items, walk, staged}} under the current tuning."""
+    arr = (U64 * 12)()
+    _check(lib().aot_graph_bins(handle, ctypes.cast(arr, P)), "aot_graph_bins")
+    return {BIN_NAMES[b]: {"pivots": arr[4 * b], "items": arr[4 * b + 1], "walk": arr[4 * b + 2],
+                           "staged": arr[4 * b + 3]} for b in range(3)}
+
+
 def aot_graph_get_tuning(handle: int) -> Tuning:
     t = Tuning()
     _check(lib().aot_graph_get_tuning(handle, ctypes.byref(t)), "aot_graph_get_tuning")
@@ -175,6 +196,24 @@ def aot_graph_get_tuning(handle: int) -> Tuning:
 def aot_graph_set_tuning(handle: int, tuning: Tuning, stream=None):
     _check(lib().aot_graph_set_tuning(handle, ctypes.byref(tuning), _stream(stream)),
            "aot_graph_set_tuning")
+
+
+def aot_kernel_launches() -> int:
+    return int(lib().aot_kernel_launches())
+
+
+def aot_profile_begin():
+    _check(lib().aot_profile_begin(), "aot_profile_begin")
+
+
+def aot_profile_end() -> dict:
+    """{kernel name: (launches, total_ms)} of the launches since aot_profile_begin."""
+    cap = 256
+    arr = (ProfileEntry * cap)()
+    cnt = I32(0)
+    _check(lib().aot_profile_end(ctypes.cast(arr, P), cap, ctypes.byref(cnt)), "aot_profile_end")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(cnt.value, cap))}
 
 
 def aot_graph_destroy(handle: int):

@@ -51,6 +51,17 @@ extern "C" aot_status aot_graph_export(const aot_graph* g, int32_t* d_perm, int3
   return AOT_OK;
 }
 
+extern "C" aot_status aot_graph_bins(const aot_graph* g, aot_bin_stats out[3]) {
+  if (!g || !out) return AOT_ERR_INVALID_ARG;
+  for (int b = 0; b < NUM_BINS; ++b) {
+    out[b].pivots = g->bin_stats[b][0];
+    out[b].items = g->bin_stats[b][1];
+    out[b].walk = g->bin_stats[b][2];
+    out[b].staged = g->bin_stats[b][3];
+  }
+  return AOT_OK;
+}
+
 extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
   if (!g || !t) return AOT_ERR_INVALID_ARG;
   t->warp_max_outdeg = g->tune.warp_max_outdeg;

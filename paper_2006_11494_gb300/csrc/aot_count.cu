@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
 
 // ------------------------------------------------------------- CTA kernel
 template <int MODE>
-__global__ void __launch_bounds__(512) k_cta_pivots(KParams P, uint32_t ts_max) {
+__global__ void __launch_bounds__(1024) k_cta_pivots(KParams P, uint32_t ts_max) {
   extern __shared__ uint32_t cta_sm[];
   uint32_t* tab = cta_sm;
   uint32_t* cnt = cta_sm + ts_max;
@@ -311,6 +311,17 @@ __global__ void k_hub_info(const uint32_t* __restrict__ pivots, uint32_t nh,
 }
 
 // ------------------------------------------------------------------ driver
+#define AOT_MODE_NAMES(k) {#k "/count", #k "/vertex", #k "/list_count", #k "/list_write"}
+static const char* const kWarpNames[4] = AOT_MODE_NAMES(k_warp_pivots);
+static const char* const kCtaNames[4] = AOT_MODE_NAMES(k_cta_pivots);
+static const char* const kHubNames[4] = AOT_MODE_NAMES(k_hub_walk);
+template <int MODE>
+static const char* mode_name(const char* base) {
+  if (base[2] == 'w') return kWarpNames[MODE];
+  if (base[2] == 'c') return kCtaNames[MODE];
+  return kHubNames[MODE];
+}
+
 static int sm_count() {
   static int sms = 0;
   if (!sms) {
@@ -334,7 +345,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     int64_t need = (nw + 7) / 8;
     if (grid > need) grid = need;
-    k_warp_pivots<MODE><<<(unsigned)grid, 256, 0, s>>>(P);
+    AOT_KERNEL(mode_name<MODE>("k_warp_pivots"), s)
+      k_warp_pivots<MODE><<<(unsigned)grid, 256, 0, s>>>(P);
     AOT_TRY(last_launch());
   }
   if (nc) {
@@ -353,19 +365,23 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cta_pivots<MODE>, threads, smem));
     int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > nc) grid = nc;
-    k_cta_pivots<MODE><<<(unsigned)grid, threads, smem, s>>>(P, ts_max);
+    AOT_KERNEL(mode_name<MODE>("k_cta_pivots"), s)
+      k_cta_pivots<MODE><<<(unsigned)grid, threads, smem, s>>>(P, ts_max);
     AOT_TRY(last_launch());
   }
   if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
     const uint32_t* dp = g->bin_pivots + nw + nc;
-    k_hub_info<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->hubinfo);
+    AOT_KERNEL("k_hub_info", s)
+      k_hub_info<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->hubinfo);
     AOT_TRY(last_launch());
     uint32_t* hp = new uint32_t[4 * (size_t)nh];
     AOT_CUDA(cudaMemcpyAsync(hp, g->hubinfo, sizeof(uint32_t) * 4 * nh, cudaMemcpyDeviceToHost, s));
     AOT_CUDA(cudaStreamSynchronize(s));
     const uint32_t words = (uint32_t)(((int64_t)g->n + 31) / 32);
     int per_group = g->tune.hub_bitmaps < MAX_HUBS ? g->tune.hub_bitmaps : MAX_HUBS;
+    // the workspace starts uninitialised; every group clears the words it set
+    AOT_CUDA(cudaMemsetAsync(g->hub_bitmap, 0, sizeof(uint32_t) * (size_t)words * per_group, s));
     for (uint32_t h0 = 0; h0 < nh; h0 += per_group) {
       HubGroup G;
       G.count = (int)((nh - h0) < (uint32_t)per_group ? (nh - h0) : (uint32_t)per_group);
@@ -383,7 +399,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
       }
       dim3 sgrid((maxdeg + 255) / 256 < 64 ? (maxdeg + 255) / 256 : 64, G.count);
       if (sgrid.x == 0) sgrid.x = 1;
-      k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, true);
+      AOT_KERNEL("k_hub_bits", s)
+        k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, true);
       AOT_TRY(last_launch());
       int per_sm = 0;
       AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hub_walk<MODE>, 256, 0));
@@ -391,9 +408,11 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
       int64_t need = ((int64_t)G.cbeg[G.count] + 7) / 8;
       if (grid > need) grid = need;
       if (grid < 1) grid = 1;
-      k_hub_walk<MODE><<<(unsigned)grid, 256, 0, s>>>(P, G);
+      AOT_KERNEL(mode_name<MODE>("k_hub_walk"), s)
+        k_hub_walk<MODE><<<(unsigned)grid, 256, 0, s>>>(P, G);
       AOT_TRY(last_launch());
-      k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, false);
+      AOT_KERNEL("k_hub_bits", s)
+        k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, false);
       AOT_TRY(last_launch());
     }
     delete[] hp;
@@ -468,7 +487,8 @@ extern "C" aot_status aot_count_per_vertex(aot_graph* g, aot_route route, uint64
   if (g->n > 0) {
     AOT_CUDA(cudaMemsetAsync(g->tv, 0, sizeof(uint64_t) * g->n, s));
     if (g->m > 0) AOT_TRY(launch_bins<M_VERTEX>(g, base_params(g), s));
-    k_gather_counts<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(g->tv, g->rank, g->n, d_counts);
+    AOT_KERNEL("k_gather_counts", s)
+      k_gather_counts<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(g->tv, g->rank, g->n, d_counts);
     AOT_TRY(last_launch());
   }
   if (h_total) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -32,6 +33,17 @@ constexpr uint32_t DEVERR_TIMEOUT = 4u;  // a bounded wait ran out
 inline aot_status last_launch() {
   return cudaGetLastError() == cudaSuccess ? AOT_OK : AOT_ERR_CUDA;
 }
+
+// Launch accounting: AOT_KERNEL(name, stream) <launch statement>;
+// counts the launch and, while profiling is on, brackets it with events.
+struct ProfScope {
+  bool once = true;
+  int slot = -1;
+  cudaStream_t s;
+  ProfScope(const char* name, cudaStream_t st);
+  ~ProfScope();
+};
+#define AOT_KERNEL(name, stream) for (aot::ProfScope ps_(name, stream); ps_.once; ps_.once = false)
 
 // Bump allocator over a caller-owned device workspace.  With base == nullptr
 // it only measures (used by the *_workspace_size queries).
@@ -114,6 +126,7 @@ struct DevScalars {  // small device-resident scalars
   unsigned long long aux[7];
   unsigned int err;              // error word
   unsigned int counters[15];     // work-queue cursors
+  unsigned long long bins[4 * 3];  // per bin: pivots, items, walk, staged deg+
 };
 
 }  // namespace aot
@@ -153,6 +166,7 @@ struct aot_graph {
   uint64_t list_total = 0;
   // bins (host copy of counts), valid for the thresholds in `binned_for`
   uint32_t bin_count[aot::NUM_BINS] = {0, 0, 0};
+  uint64_t bin_stats[aot::NUM_BINS][4] = {};  // pivots, items, walk, staged
   uint32_t binned_warp_max = 0, binned_cta_max = 0;
   aot::Tuning tune;
 };

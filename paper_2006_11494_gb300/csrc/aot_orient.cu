@@ -206,6 +206,25 @@ __global__ void k_bin_scatter(const uint32_t* __restrict__ flag, const uint32_t*
   if (flag[p]) out[base + pos[p]] = (uint32_t)p;
 }
 
+__global__ void k_bin_stats(const uint32_t* __restrict__ items, const uint32_t* __restrict__ outdeg,
+                            const uint64_t* __restrict__ walk, int32_t n, uint32_t warp_max,
+                            uint32_t cta_max, DevScalars* dev) {
+  __shared__ unsigned long long acc[4 * NUM_BINS];
+  if (threadIdx.x < 4 * NUM_BINS) acc[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && items[p] > 0) {
+    uint32_t d = outdeg[p];
+    int b = d <= warp_max ? BIN_WARP : (d <= cta_max ? BIN_CTA : BIN_HUB);
+    atomicAdd(&acc[4 * b + 0], 1ull);
+    atomicAdd(&acc[4 * b + 1], (unsigned long long)items[p]);
+    atomicAdd(&acc[4 * b + 2], (unsigned long long)walk[p]);
+    atomicAdd(&acc[4 * b + 3], (unsigned long long)d);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * NUM_BINS && acc[threadIdx.x]) atomicAdd(&dev->bins[threadIdx.x], acc[threadIdx.x]);
+}
+
 static inline unsigned grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return (unsigned)(g < 1 ? 1 : g);
@@ -217,12 +236,14 @@ aot_status bin_pivots(aot_graph* g, cudaStream_t s) {
   for (int b = 0; b < NUM_BINS; ++b) {
     uint32_t cnt = 0;
     if (g->n > 0) {
-      k_bin_flags<<<grid_for(g->n, T), T, 0, s>>>(g->items, g->outdeg, g->n,
+      AOT_KERNEL("k_bin_flags", s)
+        k_bin_flags<<<grid_for(g->n, T), T, 0, s>>>(g->items, g->outdeg, g->n,
                                                   g->tune.warp_max_outdeg,
                                                   g->tune.cta_max_outdeg, b, g->bin_flag);
       AOT_TRY(last_launch());
       AOT_TRY(scan_u32_u32(g->bin_flag, g->bin_pos, g->n, g->scan_tmp, s));
-      k_bin_scatter<<<grid_for(g->n, T), T, 0, s>>>(g->bin_flag, g->bin_pos, g->n, base,
+      AOT_KERNEL("k_bin_scatter", s)
+        k_bin_scatter<<<grid_for(g->n, T), T, 0, s>>>(g->bin_flag, g->bin_pos, g->n, base,
                                                     g->bin_pivots);
       AOT_TRY(last_launch());
       AOT_CUDA(cudaMemcpyAsync(&cnt, g->bin_pos + g->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -231,6 +252,19 @@ aot_status bin_pivots(aot_graph* g, cudaStream_t s) {
     g->bin_count[b] = cnt;
     base += cnt;
   }
+  AOT_CUDA(cudaMemsetAsync(g->dev->bins, 0, sizeof(g->dev->bins), s));
+  if (g->n > 0) {
+    AOT_KERNEL("k_bin_stats", s)
+      k_bin_stats<<<grid_for(g->n, T), T, 0, s>>>(g->items, g->outdeg, g->walk, g->n,
+                                                  g->tune.warp_max_outdeg, g->tune.cta_max_outdeg,
+                                                  g->dev);
+    AOT_TRY(last_launch());
+  }
+  unsigned long long hb[4 * NUM_BINS];
+  AOT_CUDA(cudaMemcpyAsync(hb, g->dev->bins, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  AOT_CUDA(cudaStreamSynchronize(s));
+  for (int b = 0; b < NUM_BINS; ++b)
+    for (int k = 0; k < 4; ++k) g->bin_stats[b][k] = hb[4 * b + k];
   g->binned_warp_max = g->tune.warp_max_outdeg;
   g->binned_cta_max = g->tune.cta_max_outdeg;
   return AOT_OK;
@@ -369,12 +403,14 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   uint64_t* sorted = L.keysA;
   uint64_t* other = L.keysB;
   if (E > 0) {
-    k_make_keys<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, L.dev);
+    AOT_KERNEL("k_make_keys", s)
+      k_make_keys<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     aot_status st = radix_sort_u64(L.keysA, L.keysB, E, 2 * bits, L.tmp, s, &sorted);
     if (st) return fail(st);
     other = sorted == L.keysA ? L.keysB : L.keysA;
-    k_unique_flags<<<grid_for(E, T), T, 0, s>>>(sorted, E, L.flags);
+    AOT_KERNEL("k_unique_flags", s)
+      k_unique_flags<<<grid_for(E, T), T, 0, s>>>(sorted, E, L.flags);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     st = scan_u32_u32(L.flags, L.pos, E, L.tmp, s);
     if (st) return fail(st);
@@ -385,19 +421,22 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     st = read_device_error(g, s);
     if (st) return fail(st);
     m = mm;
-    k_compact_unique<<<grid_for(E, T), T, 0, s>>>(sorted, L.flags, L.pos, E, bits, other, L.deg);
+    AOT_KERNEL("k_compact_unique", s)
+      k_compact_unique<<<grid_for(E, T), T, 0, s>>>(sorted, L.flags, L.pos, E, bits, other, L.deg);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   g->m = m;
   // 2. eta: stable sort of ids by degree key
   if (n > 0) {
-    k_eta_keys<<<grid_for(n, T), T, 0, s>>>(L.deg, n, bits, !(flags & AOT_ETA_DEG_ASC), L.ek0,
+    AOT_KERNEL("k_eta_keys", s)
+      k_eta_keys<<<grid_for(n, T), T, 0, s>>>(L.deg, n, bits, !(flags & AOT_ETA_DEG_ASC), L.ek0,
                                             L.ev0);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     uint32_t *ko, *vo;
     aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, s, &ko, &vo);
     if (st) return fail(st);
-    k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.perm, L.rank);
+    AOT_KERNEL("k_rank_from_perm", s)
+      k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.perm, L.rank);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   // 3. orient: relabel, sort, split into out-CSR
@@ -405,18 +444,21 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (m > 0) {
     uint64_t* ukeys = other;
     uint64_t* okeys = sorted;  // reuse the other buffer
-    k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, okeys);
+    AOT_KERNEL("k_relabel", s)
+      k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, okeys);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     uint64_t* osorted;
     aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, s, &osorted);
     if (st) return fail(st);
-    k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, L.adj, esrc, L.outdeg);
+    AOT_KERNEL("k_split_csr", s)
+      k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, L.adj, esrc, L.outdeg);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
     aot_status st = scan_u32_u32(L.outdeg, L.off, n, L.tmp, s);
     if (st) return fail(st);
-    k_max_outdeg<<<grid_for(n, T), T, 0, s>>>(L.outdeg, n, L.dev);
+    AOT_KERNEL("k_max_outdeg", s)
+      k_max_outdeg<<<grid_for(n, T), T, 0, s>>>(L.outdeg, n, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   } else {
     if (cudaMemsetAsync(L.off, 0, sizeof(uint32_t), s)) return fail(AOT_ERR_CUDA);
@@ -426,7 +468,8 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   g->wvert = reinterpret_cast<uint32_t*>(L.keysB);
   g->wedge = reinterpret_cast<uint32_t*>(L.keysB) + (E > 0 ? E : 1);
   if (m > 0) {
-    k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items);
+    AOT_KERNEL("k_item_count", s)
+      k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
@@ -437,12 +480,14 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     if (cudaMemsetAsync(L.wofs, 0, sizeof(uint32_t), s)) return fail(AOT_ERR_CUDA);
   }
   if (m > 0) {
-    k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, L.bin_flag,
+    AOT_KERNEL("k_item_fill", s)
+      k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, L.bin_flag,
                                              g->witem, g->wvert, g->wedge);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
-    k_pivot_walk<<<grid_for((int64_t)n * 32, T), T, 0, s>>>(L.wofs, g->witem, L.outdeg, n, L.walk,
+    AOT_KERNEL("k_pivot_walk", s)
+      k_pivot_walk<<<grid_for((int64_t)n * 32, T), T, 0, s>>>(L.wofs, g->witem, L.outdeg, n, L.walk,
                                                            L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }

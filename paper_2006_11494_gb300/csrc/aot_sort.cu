@@ -103,15 +103,18 @@ static aot_status scan_impl(const Tin* in, Tout* out, int64_t N, char* tmp, cuda
   }
   int64_t tiles = (N + SCAN_TILE - 1) / SCAN_TILE;
   if (tiles == 1) {
-    k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, N, nullptr, out);
+    AOT_KERNEL("k_tile_scan", s)
+      k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, N, nullptr, out);
     return last_launch();
   }
   Tout* sums = reinterpret_cast<Tout*>(tmp);
   char* next = tmp + (((size_t)(tiles + 1) * 8 + 255) & ~size_t(255));
-  k_tile_reduce<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, N, sums);
+  AOT_KERNEL("k_tile_reduce", s)
+    k_tile_reduce<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, N, sums);
   AOT_TRY(last_launch());
   AOT_TRY((scan_impl<Tout, Tout>(sums, sums, tiles, next, s)));
-  k_tile_scan<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, N, sums, out);
+  AOT_KERNEL("k_tile_scan", s)
+    k_tile_scan<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, N, sums, out);
   return last_launch();
 }
 
@@ -271,10 +274,12 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
   uint32_t* va = vals;
   uint32_t* vb = vals_alt;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<K><<<(unsigned)tiles, RS_THREADS, 0, s>>>(a, N, shift, hist, tiles);
+    AOT_KERNEL("k_radix_hist", s)
+      k_radix_hist<K><<<(unsigned)tiles, RS_THREADS, 0, s>>>(a, N, shift, hist, tiles);
     AOT_TRY(last_launch());
     AOT_TRY(scan_u32_u32(hist, offs, (int64_t)RS_BUCKETS * tiles, stmp, s));
-    k_radix_scatter<K, VALS><<<(unsigned)tiles, RS_THREADS, smem, s>>>(a, va, N, shift, offs,
+    AOT_KERNEL("k_radix_scatter", s)
+      k_radix_scatter<K, VALS><<<(unsigned)tiles, RS_THREADS, smem, s>>>(a, va, N, shift, offs,
                                                                          tiles, b, vb);
     AOT_TRY(last_launch());
     K* t = a; a = b; b = t;
