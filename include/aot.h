@@ -196,6 +196,35 @@ aot_status aot_profile_begin(void);
  * distinct kernels. */
 aot_status aot_profile_end(aot_profile_entry* out, int32_t cap, int32_t* count);
 
+/* ---- counting without device allocation ----
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory (no cudaMalloc allowed where they run,
+ * or a memory budget owned by a host framework that only hands out its input
+ * and output buffers) and therefore cannot supply the workspace the other
+ * entry points need.  Its scratch memory is a fixed __device__ array of
+ * AOT_STATIC_SCRATCH_BYTES inside libaot.so, held by every GPU that loads the
+ * library until the process exits.
+ *
+ * Same result as aot_orient(..., AOT_FLAG_NO_LIST, ...) followed by
+ * aot_count_per_vertex (or aot_count when d_counts is NULL) with the plain
+ * route: *h_total = T and, if d_counts != NULL, d_counts[n] = t(v) (uint64,
+ * original ids).  Synchronises s.  The call makes no cudaMalloc / cudaFree
+ * and uses no allocating library routine.
+ * Limit: the workspace that aot_orient_workspace_size reports for
+ * (num_edges, num_vertices, AOT_FLAG_NO_LIST) must fit the array, else the
+ * call returns AOT_ERR_OVERFLOW and does nothing (e.g. 262,144 pairs over
+ * 16,384 vertices fit in 8.6 MB; 1,200,000 pairs over 65,536 vertices need
+ * more than 32 MB and are rejected).
+ * The first call on a device (run with that device current) looks up the
+ * array's device address and caches it: make that first call before any
+ * stream capture.  All calls share the array, which keeps the last call's
+ * contents (each call re-initialises what must start at zero): calls that
+ * overlap on the GPU race, so serialise them. */
+#define AOT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+aot_status aot_count_per_vertex_static(const int32_t* d_src, const int32_t* d_dst,
+                                       int64_t num_edges, int32_t num_vertices,
+                                       uint64_t* d_counts, uint64_t* h_total, aot_stream_t s);
+
 /* Free the host handle (the workspace stays with the caller). */
 aot_status aot_graph_destroy(aot_graph* g);
 

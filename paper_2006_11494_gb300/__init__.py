@@ -50,6 +50,7 @@ SIGNATURES = {
     "aot_graph_get_tuning": (ctypes.c_int, [P, P]),
     "aot_graph_set_tuning": (ctypes.c_int, [P, P, P]),
     "aot_graph_destroy": (ctypes.c_int, [P]),
+    "aot_count_per_vertex_static": (ctypes.c_int, [P, P, I64, I32, P, ctypes.POINTER(U64), P]),
     "aot_kernel_launches": (ctypes.c_ulonglong, []),
     "aot_profile_begin": (ctypes.c_int, []),
     "aot_profile_end": (ctypes.c_int, [P, I32, ctypes.POINTER(I32)]),
@@ -196,6 +197,19 @@ def aot_graph_get_tuning(handle: int) -> Tuning:
 def aot_graph_set_tuning(handle: int, tuning: Tuning, stream=None):
     _check(lib().aot_graph_set_tuning(handle, ctypes.byref(tuning), _stream(stream)),
            "aot_graph_set_tuning")
+
+
+STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def aot_count_per_vertex_static(src, dst, num_vertices: int, counts=None, stream=None) -> int:
+    """Per-vertex count with no device allocation (scratch is a fixed device
+    array inside the library); returns T and fills ``counts`` if given."""
+    t = U64(0)
+    _check(lib().aot_count_per_vertex_static(_ptr(src), _ptr(dst), src.numel(), num_vertices,
+                                             _ptr(counts), ctypes.byref(t), _stream(stream)),
+           "aot_count_per_vertex_static")
+    return t.value
 
 
 def aot_kernel_launches() -> int:
