@@ -146,7 +146,10 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * deg+ <= warp_max_outdeg -> one warp per pivot (hash table in the warp's
  * shared memory; warp_max_outdeg <= 64), deg+ <= cta_max_outdeg -> one CTA
  * per pivot (shared-memory hash table; cta_max_outdeg <= 8192), larger ->
- * hub path (global bitmaps of n bits, hub_bitmaps of them at a time, 1..64).
+ * hub path.  hub_mode 0: a shared-memory bitmap over eta ranks, swept one
+ * segment of seg_bits ranks at a time (a multiple of 32 in [1024, 1572864])
+ * by a CTA per (pivot, block of 2048 items); hub_mode 1: global bitmaps of
+ * n bits, hub_bitmaps (1..32) hubs at a time, all CTAs sharing their items.
  * cta_threads is a multiple of 32 in [64, 1024].  Tuning never changes
  * results, only speed. */
 typedef struct {
@@ -154,6 +157,8 @@ typedef struct {
   uint32_t cta_max_outdeg;
   int32_t cta_threads;
   int32_t hub_bitmaps;
+  int32_t hub_mode;
+  uint32_t seg_bits;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

@@ -68,6 +68,8 @@ extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
   t->cta_max_outdeg = g->tune.cta_max_outdeg;
   t->cta_threads = g->tune.cta_threads;
   t->hub_bitmaps = g->tune.hub_bitmaps;
+  t->hub_mode = g->tune.hub_mode;
+  t->seg_bits = g->tune.seg_bits;
   return AOT_OK;
 }
 
@@ -75,13 +77,17 @@ extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, ao
   if (!g || !t) return AOT_ERR_INVALID_ARG;
   if (t->warp_max_outdeg > 64 || t->cta_max_outdeg > 8192 ||
       t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
-      (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps)
+      (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
+      t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
+      (t->seg_bits & 31))
     return AOT_ERR_INVALID_ARG;
   Tuning old = g->tune;
   g->tune.warp_max_outdeg = t->warp_max_outdeg;
   g->tune.cta_max_outdeg = t->cta_max_outdeg;
   g->tune.cta_threads = t->cta_threads;
   g->tune.hub_bitmaps = t->hub_bitmaps;
+  g->tune.hub_mode = t->hub_mode;
+  g->tune.seg_bits = t->seg_bits;
   aot_status st = bin_pivots(g, reinterpret_cast<cudaStream_t>(stream));
   if (st != AOT_OK) g->tune = old;
   return st;

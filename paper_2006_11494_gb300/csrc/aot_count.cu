@@ -23,7 +23,7 @@
 namespace aot {
 
 enum Mode { M_COUNT = 0, M_VERTEX = 1, M_LIST_COUNT = 2, M_LIST_WRITE = 3 };
-enum Queue { Q_WARP = 1, Q_CTA = 2, Q_HUB = 3 };
+enum Queue { Q_WARP = 1, Q_CTA = 2, Q_HUB = 3, Q_SEG = 4 };
 
 struct KParams {
   const uint32_t* off;
@@ -64,9 +64,26 @@ __device__ __forceinline__ int clamp_lane(int64_t x) {
   return x < -1 ? -1 : (x > 64 ? 64 : (int)x);
 }
 
+// Listing output: triangle number idx, if it falls in the window, as
+// (x, y, w) in original ids with eta(x) < eta(y) < eta(w).
+__device__ __forceinline__ void emit(const KParams& P, uint64_t idx, uint32_t p, uint32_t v,
+                                     uint32_t w) {
+  if (idx >= P.cursor && idx < P.cursor + P.cap) {
+    int32_t* o = P.out + 3 * (idx - P.cursor);
+    o[0] = P.perm[p < v ? p : v];
+    o[1] = P.perm[p < v ? v : p];
+    o[2] = P.perm[w];
+  }
+}
+
+constexpr uint32_t LONG_ITEM = 64;  // items at least this long are walked by the whole warp
+
 // One warp walks items [c, min(c+32, ie)) of pivot p.  probe(w, slot) tests
 // H; on_w(w, slot) is called by every hitting lane (per-vertex counts of w).
-// Returns this lane's number of hits.
+// Long items are walked one at a time by all 32 lanes, four loads in flight
+// per lane; the short ones are flattened: lanes take consecutive positions
+// of their concatenated walk ranges and find their item by a shuffle search
+// over the exclusive prefix of the lengths.  Returns this lane's hit count.
 template <int MODE, class Probe, class OnW>
 __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uint32_t c,
                                                uint32_t ie, Probe probe, OnW on_w) {
@@ -83,12 +100,53 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
     if (a == b || b <= P.cursor || a >= P.cursor + P.cap) r.y = r.x;  // nothing in the window
     tbase = a;
   }
-  const uint32_t len = r.y - r.x;
+  uint32_t len = r.y - r.x;
+  uint32_t ihits = 0;  // hits of the item held by this lane
+  uint32_t my = 0;     // hits found by this lane
+
+  // ---- long items: the whole warp, 4 x 32 entries per step
+  unsigned longm = __ballot_sync(FULL, len >= LONG_ITEM);
+  while (longm) {
+    const int j = __ffs(longm) - 1;
+    longm &= longm - 1;
+    const uint32_t x = __shfl_sync(FULL, r.x, j), y = __shfl_sync(FULL, r.y, j);
+    uint32_t vj = 0;
+    uint64_t tb = 0;
+    if (MODE == M_LIST_WRITE) {
+      vj = __shfl_sync(FULL, vert, j);
+      tb = ((uint64_t)__shfl_sync(FULL, (uint32_t)(tbase >> 32), j) << 32) |
+           __shfl_sync(FULL, (uint32_t)tbase, j);
+    }
+    uint32_t h = 0;  // hits of item j so far (warp-uniform)
+    for (uint32_t k = x; k < y; k += 128) {
+      uint32_t w[4], slot[4];
+      bool hit[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t idx = k + u * 32 + lane;
+        w[u] = idx < y ? __ldg(P.adj + idx) : EMPTY;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) hit[u] = w[u] != EMPTY && probe(w[u], slot[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned hm = __ballot_sync(FULL, hit[u]);
+        if (hit[u]) {
+          ++my;
+          if (MODE == M_VERTEX) on_w(w[u], slot[u]);
+          if (MODE == M_LIST_WRITE) emit(P, tb + h + (uint32_t)__popc(hm & lanemask_lt()), p, vj, w[u]);
+        }
+        h += (uint32_t)__popc(hm);
+      }
+    }
+    if ((int)lane == j) ihits = h;
+  }
+  if (len >= LONG_ITEM) len = 0;
+
+  // ---- short items: flattened
   const uint32_t incl = warp_inclusive_scan(len);
   const uint32_t total = __shfl_sync(FULL, incl, 31);
   const uint32_t excl = incl - len;
-  uint32_t ihits = 0;  // hits of the item held by this lane
-  uint32_t my = 0;     // hits found by this lane
   for (uint32_t q0 = 0; q0 < total; q0 += 32) {
     const uint32_t q = q0 + lane;
     const bool act = q < total;
@@ -113,16 +171,9 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
       const uint32_t tb_lo = __shfl_sync(FULL, (uint32_t)tbase, j);
       const uint32_t tb_hi = __shfl_sync(FULL, (uint32_t)(tbase >> 32), j);
       const uint32_t vj = __shfl_sync(FULL, vert, j);
-      if (hit) {
-        uint64_t idx = (((uint64_t)tb_hi << 32) | tb_lo) + prev +
-                       (uint32_t)__popc(hm & peers & lanemask_lt());
-        if (idx >= P.cursor && idx < P.cursor + P.cap) {
-          int32_t* o = P.out + 3 * (idx - P.cursor);
-          o[0] = P.perm[p < vj ? p : vj];
-          o[1] = P.perm[p < vj ? vj : p];
-          o[2] = P.perm[w];
-        }
-      }
+      if (hit)
+        emit(P, (((uint64_t)tb_hi << 32) | tb_lo) + prev + (uint32_t)__popc(hm & peers & lanemask_lt()),
+             p, vj, w);
     }
     if (MODE != M_COUNT) {
       const int64_t lo = (int64_t)excl - (int64_t)q0, hi = (int64_t)incl - (int64_t)q0;
@@ -197,7 +248,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
 
 // ------------------------------------------------------------- CTA kernel
 template <int MODE>
-__global__ void __launch_bounds__(1024) k_cta_pivots(KParams P, uint32_t ts_max) {
+__global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_max) {
   extern __shared__ uint32_t cta_sm[];
   uint32_t* tab = cta_sm;
   uint32_t* cnt = cta_sm + ts_max;
@@ -298,6 +349,199 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
   if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
 }
 
+// ------------------------------------------------ segmented bitmap kernel
+// Pivots with a large deg+ (beyond the shared-memory hash tables): H is a
+// bitmap over eta ranks, held in shared memory one segment of SEG_BITS ranks
+// at a time.  A CTA owns (pivot, block of up to SEG_ITEMS items) and sweeps
+// the pivot's rank range [min N+(p), max N+(p)] segment by segment: it sets
+// the bits of N+(p) in the segment, every warp advances its items' cursors
+// through the entries below the segment end (out-lists are sorted by eta, so
+// each walked entry is visited exactly once over all segments), then clears
+// the bits.  Items keep cursor, end and hit count in shared memory, so one
+// item's hits come out in ascending w order (the listing order).
+constexpr int SEG_THREADS = 1024;
+constexpr uint32_t SEG_ITEMS = 2048;
+constexpr uint32_t SEG_BITS_MAX = 1536u * 1024u;  // 192 KB of bitmap at most
+constexpr size_t seg_smem_bytes(uint32_t seg_bits) {
+  return (size_t)(seg_bits / 32) * 4 + 3 * (size_t)SEG_ITEMS * 4;
+}
+
+__global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
+                                  const uint32_t* __restrict__ wofs, uint32_t* __restrict__ cnt) {
+  uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nh) return;
+  uint32_t p = pivots[h];
+  cnt[h] = (wofs[p + 1] - wofs[p] + SEG_ITEMS - 1) / SEG_ITEMS;
+}
+
+// first index in [lo, hi) with a[idx] >= key (a sorted); all 32 lanes call it
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict__ a, uint32_t lo,
+                                                     uint32_t hi, uint32_t key) {
+  const unsigned lane = lane_id();
+  while (hi - lo > 32) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t idx = lo + lane * step;
+    const bool less = idx < hi && a[idx] < key;
+    const int c = __popc(__ballot_sync(FULL, less));
+    if (c == 0) return lo;
+    const uint32_t nlo = lo + (uint32_t)(c - 1) * step + 1;
+    const uint32_t nhi = min(hi, lo + (uint32_t)c * step);
+    lo = nlo;
+    hi = nhi;
+  }
+  const uint32_t idx = lo + lane;
+  const bool less = idx < hi && a[idx] < key;
+  return lo + (uint32_t)__popc(__ballot_sync(FULL, less));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
+                                                               uint32_t nh, uint32_t SEG_BITS) {
+  extern __shared__ uint32_t seg_sm[];
+  const uint32_t SEG_WORDS = SEG_BITS / 32;
+  uint32_t* bm = seg_sm;
+  uint32_t* cur = bm + SEG_WORDS;
+  uint32_t* endp = cur + SEG_ITEMS;
+  uint32_t* ih = endp + SEG_ITEMS;
+  __shared__ uint32_t s_task, s_hub, s_pe, s_next;
+  __shared__ unsigned long long s_hits;
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
+  const uint32_t ntasks = task_ofs[nh];
+  for (uint32_t i = threadIdx.x; i < SEG_WORDS; i += blockDim.x) bm[i] = 0;
+  uint64_t found = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_task = atomicAdd(&P.dev->counters[Q_SEG], 1u);
+      s_hits = 0;
+    }
+    __syncthreads();
+    const uint32_t task = s_task;
+    if (task >= ntasks) break;
+    if (wid == 0) {  // largest h with task_ofs[h] <= task (32-ary search)
+      uint32_t lo = 0, hi = nh;
+      while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + lane * step;
+        const bool le = idx < hi && task_ofs[idx] <= task;
+        const int c = __popc(__ballot_sync(FULL, le));
+        const uint32_t nlo = lo + (uint32_t)(c - 1) * step;
+        const uint32_t nhi = min(hi, lo + (uint32_t)c * step);
+        lo = nlo;
+        hi = nhi;
+      }
+      if (lane == 0) s_hub = lo;
+    }
+    __syncthreads();
+    const uint32_t h = s_hub;
+    const uint32_t p = P.pivots[h];
+    const uint32_t i0 = P.wofs[p] + (task - task_ofs[h]) * SEG_ITEMS;
+    const uint32_t i1 = min(i0 + SEG_ITEMS, P.wofs[p + 1]);
+    const uint32_t nk = i1 - i0;
+    for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+      uint2 r = P.witem[i0 + k];
+      if (MODE == M_LIST_WRITE) {
+        const uint32_t e = P.wedge[i0 + k];
+        const uint64_t a = P.toff[e], b = P.toff[e + 1];
+        if (a == b || b <= P.cursor || a >= P.cursor + P.cap) r.y = r.x;
+      }
+      cur[k] = r.x;
+      endp[k] = r.y;
+      ih[k] = 0;
+    }
+    const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
+    const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
+    uint32_t pc = pbeg;
+    __syncthreads();
+    for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += SEG_BITS) {
+      const uint32_t segHi = min(segLo + SEG_BITS, hi_rank);
+      if (wid == 0) {
+        const uint32_t pe = warp_lower_bound(P.adj, pc, pend, segHi);
+        if (lane == 0) s_pe = pe;
+      }
+      if (threadIdx.x == 0) s_next = 0;
+      __syncthreads();
+      const uint32_t pe = s_pe;
+      if (pe > pc) {
+        for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
+          const uint32_t b = P.adj[k] - segLo;
+          atomicOr(&bm[b >> 5], 1u << (b & 31));
+        }
+        __syncthreads();
+        while (true) {
+          uint32_t k = 0;
+          if (lane == 0) k = atomicAdd(&s_next, 1u);
+          k = __shfl_sync(FULL, k, 0);
+          if (k >= nk) break;
+          uint32_t x = cur[k];
+          const uint32_t y = endp[k];
+          uint32_t hk = ih[k];
+          uint32_t vj = 0;
+          uint64_t tb = 0;
+          if (MODE == M_LIST_WRITE && x < y) {
+            vj = P.wvert[i0 + k];
+            tb = P.toff[P.wedge[i0 + k]];
+          }
+          while (x < y) {
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t idx = x + u * 32 + lane;
+              w[u] = idx < y ? __ldg(P.adj + idx) : EMPTY;
+            }
+            uint32_t consumed = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const bool in = w[u] < segHi;
+              consumed += (uint32_t)__popc(__ballot_sync(FULL, in));
+              bool hit = false;
+              if (in && w[u] >= segLo) {
+                const uint32_t b = w[u] - segLo;
+                hit = (bm[b >> 5] >> (b & 31)) & 1u;
+              }
+              const unsigned hm = __ballot_sync(FULL, hit);
+              if (hit) {
+                ++found;
+                if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[u]], 1ull);
+                if (MODE == M_LIST_WRITE) emit(P, tb + hk + (uint32_t)__popc(hm & lanemask_lt()), p, vj, w[u]);
+              }
+              hk += (uint32_t)__popc(hm);
+            }
+            x += consumed;
+            if (consumed < 128) break;
+          }
+          if (lane == 0) {
+            cur[k] = x;
+            ih[k] = hk;
+          }
+        }
+        __syncthreads();
+        for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
+          const uint32_t b = P.adj[k] - segLo;
+          bm[b >> 5] = 0u;
+        }
+      }
+      pc = pe;
+      __syncthreads();
+    }
+    uint32_t th = 0;
+    for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+      const uint32_t hk = ih[k];
+      th += hk;
+      if (MODE == M_VERTEX && hk) atomicAdd((unsigned long long*)&P.tv[P.wvert[i0 + k]], (unsigned long long)hk);
+      if (MODE == M_LIST_COUNT) P.tcnt[P.wedge[i0 + k]] = hk;
+    }
+    if (MODE == M_VERTEX) {
+      th = warp_sum(th);
+      if (lane == 0 && th) atomicAdd(&s_hits, (unsigned long long)th);
+      __syncthreads();
+      if (threadIdx.x == 0 && s_hits) atomicAdd((unsigned long long*)&P.tv[p], s_hits);
+    }
+    __syncthreads();
+  }
+  found = warp_sum(found);
+  if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
+}
+
 __global__ void k_hub_info(const uint32_t* __restrict__ pivots, uint32_t nh,
                            const uint32_t* __restrict__ wofs, const uint32_t* __restrict__ off,
                            uint32_t* __restrict__ info) {
@@ -315,10 +559,12 @@ __global__ void k_hub_info(const uint32_t* __restrict__ pivots, uint32_t nh,
 static const char* const kWarpNames[4] = AOT_MODE_NAMES(k_warp_pivots);
 static const char* const kCtaNames[4] = AOT_MODE_NAMES(k_cta_pivots);
 static const char* const kHubNames[4] = AOT_MODE_NAMES(k_hub_walk);
+static const char* const kSegNames[4] = AOT_MODE_NAMES(k_seg_pivots);
 template <int MODE>
 static const char* mode_name(const char* base) {
   if (base[2] == 'w') return kWarpNames[MODE];
   if (base[2] == 'c') return kCtaNames[MODE];
+  if (base[2] == 's') return kSegNames[MODE];
   return kHubNames[MODE];
 }
 
@@ -369,7 +615,32 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
       k_cta_pivots<MODE><<<(unsigned)grid, threads, smem, s>>>(P, ts_max);
     AOT_TRY(last_launch());
   }
-  if (nh) {
+  if (nh && g->tune.hub_mode == 0) {
+    // segmented shared-memory bitmap: tasks = (pivot, block of SEG_ITEMS items)
+    const uint32_t* dp = g->bin_pivots + nw + nc;
+    uint32_t* cnt = g->hubinfo;
+    uint32_t* task_ofs = g->hubinfo + g->n;
+    AOT_KERNEL("k_seg_task_counts", s)
+      k_seg_task_counts<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, cnt);
+    AOT_TRY(last_launch());
+    AOT_TRY(scan_u32_u32(cnt, task_ofs, nh, g->scan_tmp, s));
+    const uint32_t seg_bits = g->tune.seg_bits;
+    const size_t seg_smem = seg_smem_bytes(seg_bits);
+    static bool seg_attr[4] = {false, false, false, false};
+    if (!seg_attr[MODE]) {
+      AOT_CUDA(cudaFuncSetAttribute(k_seg_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)seg_smem_bytes(SEG_BITS_MAX)));
+      seg_attr[MODE] = true;
+    }
+    P.pivots = dp;
+    P.num_pivots = nh;
+    int per_sm = 0;
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
+    AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
+      k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
+          P, task_ofs, nh, seg_bits);
+    AOT_TRY(last_launch());
+  } else if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
     const uint32_t* dp = g->bin_pivots + nw + nc;
     AOT_KERNEL("k_hub_info", s)

@@ -119,6 +119,8 @@ struct Tuning {
   int cta_threads = 512;
   int warp_cta_threads = 256;
   int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)
+  int hub_mode = 0;                 // 0: segmented shared-memory bitmap, 1: global bitmaps
+  uint32_t seg_bits = 1536u * 1024u;  // ranks per shared-memory bitmap segment (hub_mode 0)
 };
 
 struct DevScalars {  // small device-resident scalars

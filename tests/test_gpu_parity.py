@@ -93,6 +93,9 @@ def test_chunglu_full_parity():
     dict(warp_max_outdeg=64, cta_max_outdeg=64),                   # warp + hub
     dict(warp_max_outdeg=1, cta_max_outdeg=8192, cta_threads=128),  # almost all CTA
     dict(warp_max_outdeg=16, cta_max_outdeg=256, cta_threads=1024, hub_bitmaps=3),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_mode=1, hub_bitmaps=7),  # global bitmaps
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, hub_mode=0, seg_bits=1024),  # many segments
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_mode=0, seg_bits=4096),
 ])
 def test_every_bin_gives_the_same_answer(tuning):
     n, s, d = gg.rmat_cfg(13, 7)
@@ -114,6 +117,24 @@ def test_hub_wheel():
     n, s, d = gg.wheel(20000)  # hub deg+ 20000: beyond the shared-memory bins
     g, ref = check_full(n, s, d)
     assert g.info["max_outdeg"] == 20000
+
+
+@pytest.mark.parametrize("hub_mode", [0, 1])
+def test_wheel_multi_segment_closed_form(hub_mode):
+    """Wheel with a 3,000,000-vertex rim: the hub's out-list spans two
+    1.5M-rank bitmap segments.  Closed form: T = rim, t(hub) = rim, t(rim) = 2."""
+    rim = 3_000_000
+    n, s, d = gg.wheel(rim)
+    g = gpu_graph(n, s, d)
+    g.set_tuning(hub_mode=hub_mode)
+    assert g.count() == rim
+    T, t = g.count_per_vertex()
+    t = u64(t)
+    assert T == rim and t[0] == rim and np.all(t[1:] == 2)
+    lst = g.list(chunk=1 << 20).cpu().numpy()
+    assert lst.shape == (rim, 3) and np.all(lst[:, 0] == 0)
+    # canonical order: hub first, then rim pairs by eta (ties by id)
+    assert np.all(np.diff(lst[:, 1]) >= 0)
 
 
 def test_complete_dense():
