@@ -362,8 +362,10 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
 constexpr int SEG_THREADS = 1024;
 constexpr uint32_t SEG_ITEMS = 2048;
 constexpr uint32_t SEG_BITS_MAX = 1536u * 1024u;  // 192 KB of bitmap at most
+constexpr uint32_t NONE = 0xffffffffu;
+// bitmap + per item: cursor, end, next walked value, hits
 constexpr size_t seg_smem_bytes(uint32_t seg_bits) {
-  return (size_t)(seg_bits / 32) * 4 + 3 * (size_t)SEG_ITEMS * 4;
+  return (size_t)(seg_bits / 32) * 4 + 4 * (size_t)SEG_ITEMS * 4;
 }
 
 __global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
@@ -394,20 +396,99 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
   return lo + (uint32_t)__popc(__ballot_sync(FULL, less));
 }
 
+// One warp advances one item through the segment [segLo, segHi): rounds of
+// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
+// 128-bit load).  An entry b = w - segLo is a hit iff b < width and its bit
+// is set; the first entry >= segHi ends the visit (lists are eta-sorted).
+// x: cursor (updated), hk: hits of the item so far (updated; listing ranks).
+__device__ __forceinline__ uint4 seg_load(const uint32_t* __restrict__ adj, uint32_t idx0, uint32_t y) {
+  return idx0 < y ? __ldg(reinterpret_cast<const uint4*>(adj + idx0)) : make_uint4(NONE, NONE, NONE, NONE);
+}
+
+// One warp advances one item through the segment [segLo, segHi): rounds of
+// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
+// 128-bit load), with the next round's load issued before the current round
+// is tested (two rounds in flight per warp).  An entry b = w - segLo is a hit
+// iff b < width and its bit is set; the first entry >= segHi ends the visit
+// (lists are eta-sorted) and its value is returned in next_val.
+// x: cursor (updated), hk: hits of the item so far (updated; listing ranks).
+template <int MODE>
+__device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t segLo,
+                                              uint32_t segHi, uint32_t& x, uint32_t y, uint32_t& hk,
+                                              uint32_t p, uint32_t vj, uint64_t tb,
+                                              uint64_t& found, uint32_t& next_val) {
+  const unsigned lane = lane_id();
+  const uint32_t width = segHi - segLo;
+  next_val = NONE;
+  if (x >= y) return;
+  uint32_t base = x & ~3u;
+  uint4 v = seg_load(P.adj, base + 4 * lane, y);
+  while (true) {
+    const uint32_t idx0 = base + 4 * lane;
+    const uint4 vn = seg_load(P.adj, idx0 + 128, y);  // prefetch the next round
+    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+    uint32_t stop = NONE, stop_val = NONE;
+    unsigned hits = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t idx = idx0 + j;
+      const bool valid = idx >= x && idx < y;
+      if (valid && e[j] >= segHi && stop == NONE) {
+        stop = idx;
+        stop_val = e[j];
+      }
+      const uint32_t b = e[j] - segLo;
+      if (valid && b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) hits |= 1u << j;
+    }
+    const uint32_t c = (uint32_t)__popc(hits);
+    found += c;
+    if (MODE == M_VERTEX) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (hits & (1u << j)) atomicAdd((unsigned long long*)&P.tv[e[j]], 1ull);
+    }
+    if (MODE == M_LIST_WRITE) {
+      const uint32_t incl = warp_inclusive_scan(c);
+      uint64_t r = tb + hk + (incl - c);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
+      hk += __shfl_sync(FULL, incl, 31);
+    } else if (MODE != M_COUNT) {
+      hk += warp_sum(c);
+    }
+    const uint32_t first_stop = __reduce_min_sync(FULL, stop);
+    if (first_stop != NONE) {
+      const unsigned owner = __ballot_sync(FULL, stop == first_stop);
+      next_val = __shfl_sync(FULL, stop_val, __ffs(owner) - 1);
+      x = first_stop;
+      return;
+    }
+    base += 128;
+    x = base;
+    if (x >= y) {
+      x = y;
+      return;
+    }
+    v = vn;
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
-                                                               uint32_t nh, uint32_t SEG_BITS) {
+                                                               uint32_t nh, uint32_t seg_bits) {
   extern __shared__ uint32_t seg_sm[];
-  const uint32_t SEG_WORDS = SEG_BITS / 32;
+  const uint32_t seg_words = seg_bits / 32;
   uint32_t* bm = seg_sm;
-  uint32_t* cur = bm + SEG_WORDS;
+  uint32_t* cur = bm + seg_words;
   uint32_t* endp = cur + SEG_ITEMS;
-  uint32_t* ih = endp + SEG_ITEMS;
+  uint32_t* nextv = endp + SEG_ITEMS;
+  uint32_t* ih = nextv + SEG_ITEMS;
   __shared__ uint32_t s_task, s_hub, s_pe, s_next;
   __shared__ unsigned long long s_hits;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
   const uint32_t ntasks = task_ofs[nh];
-  for (uint32_t i = threadIdx.x; i < SEG_WORDS; i += blockDim.x) bm[i] = 0;
+  for (uint32_t i = threadIdx.x; i < seg_words; i += blockDim.x) bm[i] = 0;
   uint64_t found = 0;
   while (true) {
     if (threadIdx.x == 0) {
@@ -446,14 +527,15 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       }
       cur[k] = r.x;
       endp[k] = r.y;
+      nextv[k] = r.x < r.y ? P.adj[r.x] : NONE;
       ih[k] = 0;
     }
     const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
     uint32_t pc = pbeg;
     __syncthreads();
-    for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += SEG_BITS) {
-      const uint32_t segHi = min(segLo + SEG_BITS, hi_rank);
+    for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += seg_bits) {
+      const uint32_t segHi = min(segLo + seg_bits, hi_rank);
       if (wid == 0) {
         const uint32_t pe = warp_lower_bound(P.adj, pc, pend, segHi);
         if (lane == 0) s_pe = pe;
@@ -472,47 +554,23 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
           if (lane == 0) k = atomicAdd(&s_next, 1u);
           k = __shfl_sync(FULL, k, 0);
           if (k >= nk) break;
-          uint32_t x = cur[k];
+          if (nextv[k] >= segHi) continue;  // nothing of this item in the segment
+          uint32_t x = cur[k], hk = ih[k], nv;
           const uint32_t y = endp[k];
-          uint32_t hk = ih[k];
           uint32_t vj = 0;
           uint64_t tb = 0;
-          if (MODE == M_LIST_WRITE && x < y) {
+          if (MODE == M_LIST_WRITE) {
             vj = P.wvert[i0 + k];
             tb = P.toff[P.wedge[i0 + k]];
           }
-          while (x < y) {
-            uint32_t w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t idx = x + u * 32 + lane;
-              w[u] = idx < y ? __ldg(P.adj + idx) : EMPTY;
-            }
-            uint32_t consumed = 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const bool in = w[u] < segHi;
-              consumed += (uint32_t)__popc(__ballot_sync(FULL, in));
-              bool hit = false;
-              if (in && w[u] >= segLo) {
-                const uint32_t b = w[u] - segLo;
-                hit = (bm[b >> 5] >> (b & 31)) & 1u;
-              }
-              const unsigned hm = __ballot_sync(FULL, hit);
-              if (hit) {
-                ++found;
-                if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[u]], 1ull);
-                if (MODE == M_LIST_WRITE) emit(P, tb + hk + (uint32_t)__popc(hm & lanemask_lt()), p, vj, w[u]);
-              }
-              hk += (uint32_t)__popc(hm);
-            }
-            x += consumed;
-            if (consumed < 128) break;
-          }
+          seg_walk_item<MODE>(P, bm, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+          __syncwarp();
           if (lane == 0) {
             cur[k] = x;
+            nextv[k] = nv;
             ih[k] = hk;
           }
+          __syncwarp();
         }
         __syncthreads();
         for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
@@ -523,18 +581,20 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       pc = pe;
       __syncthreads();
     }
-    uint32_t th = 0;
-    for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
-      const uint32_t hk = ih[k];
-      th += hk;
-      if (MODE == M_VERTEX && hk) atomicAdd((unsigned long long*)&P.tv[P.wvert[i0 + k]], (unsigned long long)hk);
-      if (MODE == M_LIST_COUNT) P.tcnt[P.wedge[i0 + k]] = hk;
-    }
-    if (MODE == M_VERTEX) {
-      th = warp_sum(th);
-      if (lane == 0 && th) atomicAdd(&s_hits, (unsigned long long)th);
-      __syncthreads();
-      if (threadIdx.x == 0 && s_hits) atomicAdd((unsigned long long*)&P.tv[p], s_hits);
+    if (MODE != M_COUNT) {
+      uint32_t th = 0;
+      for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+        const uint32_t hk = ih[k];
+        th += hk;
+        if (MODE == M_VERTEX && hk) atomicAdd((unsigned long long*)&P.tv[P.wvert[i0 + k]], (unsigned long long)hk);
+        if (MODE == M_LIST_COUNT) P.tcnt[P.wedge[i0 + k]] = hk;
+      }
+      if (MODE == M_VERTEX) {
+        th = warp_sum(th);
+        if (lane == 0 && th) atomicAdd(&s_hits, (unsigned long long)th);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_hits) atomicAdd((unsigned long long*)&P.tv[p], s_hits);
+      }
     }
     __syncthreads();
   }

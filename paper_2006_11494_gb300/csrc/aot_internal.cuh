@@ -115,7 +115,7 @@ enum Bin { BIN_WARP = 0, BIN_CTA = 1, BIN_HUB = 2, NUM_BINS = 3 };
 
 struct Tuning {
   uint32_t warp_max_outdeg = 64;    // BIN_WARP: 1..warp_max (table 2*pow2 slots)
-  uint32_t cta_max_outdeg = 4096;   // BIN_CTA: ..cta_max (smem hash)
+  uint32_t cta_max_outdeg = 1024;   // BIN_CTA: ..cta_max (smem hash)
   int cta_threads = 512;
   int warp_cta_threads = 256;
   int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)

@@ -316,7 +316,7 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
   L.ev0 = c.take<uint32_t>(ns); L.ev1 = c.take<uint32_t>(ns);
   L.perm = c.take<int32_t>(ns); L.rank = c.take<int32_t>(ns);
   L.off = c.take<uint32_t>(ns + 1);
-  L.adj = c.take<uint32_t>(Es);
+  L.adj = c.take<uint32_t>(Es + 4);  // padded: 128-bit loads may read up to 3 entries past m
   L.outdeg = c.take<uint32_t>(ns);
   L.wofs = c.take<uint32_t>(ns + 1);
   L.items = c.take<uint32_t>(ns);
