@@ -19,29 +19,9 @@
 // walk lengths, probe H, and count with __ballot_sync/__popc.
 // Work is handed out by per-bin atomic queues (persistent grids).
 #include "aot_internal.cuh"
+#include "aot_kparams.cuh"
 
 namespace aot {
-
-enum Mode { M_COUNT = 0, M_VERTEX = 1, M_LIST_COUNT = 2, M_LIST_WRITE = 3 };
-enum Queue { Q_WARP = 1, Q_CTA = 2, Q_HUB = 3, Q_SEG = 4 };
-
-struct KParams {
-  const uint32_t* off;
-  const uint32_t* adj;
-  const uint32_t* wofs;
-  const uint2* witem;
-  const uint32_t* wvert;
-  const uint32_t* wedge;
-  const uint32_t* pivots;  // this bin's pivots
-  uint32_t num_pivots;
-  uint64_t* tv;            // per-vertex counts (rank space)
-  uint32_t* tcnt;          // triangles per oriented edge
-  const uint64_t* toff;    // exclusive offsets per oriented edge
-  const int32_t* perm;
-  int32_t* out;
-  uint64_t cursor, cap;    // listing window [cursor, cursor + cap)
-  DevScalars* dev;
-};
 
 constexpr int MAX_HUBS = 64;
 struct HubGroup {
@@ -64,18 +44,6 @@ __device__ __forceinline__ int clamp_lane(int64_t x) {
   return x < -1 ? -1 : (x > 64 ? 64 : (int)x);
 }
 
-// Listing output: triangle number idx, if it falls in the window, as
-// (x, y, w) in original ids with eta(x) < eta(y) < eta(w).
-__device__ __forceinline__ void emit(const KParams& P, uint64_t idx, uint32_t p, uint32_t v,
-                                     uint32_t w) {
-  if (idx >= P.cursor && idx < P.cursor + P.cap) {
-    int32_t* o = P.out + 3 * (idx - P.cursor);
-    o[0] = P.perm[p < v ? p : v];
-    o[1] = P.perm[p < v ? v : p];
-    o[2] = P.perm[w];
-  }
-}
-
 constexpr uint32_t LONG_ITEM = 64;  // items at least this long are walked by the whole warp
 
 // One warp walks items [c, min(c+32, ie)) of pivot p.  probe(w, slot) tests
@@ -89,7 +57,7 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
                                                uint32_t ie, Probe probe, OnW on_w) {
   const unsigned lane = lane_id();
   const uint32_t it = c + lane;
-  const bool has = it < ie;
+  const bool has = it < ie && (!P.route || P.route[it] == V_PROBE);
   uint2 r = has ? P.witem[it] : make_uint2(0u, 0u);
   uint32_t vert = 0, edge = 0;
   uint64_t tbase = 0;
@@ -205,6 +173,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
     idx = __shfl_sync(FULL, idx, 0);
     if (idx >= P.num_pivots) break;
     const uint32_t p = P.pivots[idx];
+    if (P.rprobe && P.rprobe[p] == 0) continue;  // every item of p takes another route
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
     uint32_t ts = 32;
     while (ts < 2 * d) ts <<= 1;
@@ -265,6 +234,10 @@ __global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_m
     const uint32_t idx = s_idx;
     if (idx >= P.num_pivots) break;
     const uint32_t p = P.pivots[idx];
+    if (P.rprobe && P.rprobe[p] == 0) {  // every item of p takes another route
+      __syncthreads();
+      continue;
+    }
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
     uint32_t ts = 64;
     while (ts < 2 * d) ts <<= 1;
@@ -515,11 +488,17 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     __syncthreads();
     const uint32_t h = s_hub;
     const uint32_t p = P.pivots[h];
+    if (P.rprobe && P.rprobe[p] == 0) {  // every item of p takes another route
+      __syncthreads();
+      continue;
+    }
     const uint32_t i0 = P.wofs[p] + (task - task_ofs[h]) * SEG_ITEMS;
     const uint32_t i1 = min(i0 + SEG_ITEMS, P.wofs[p + 1]);
     const uint32_t nk = i1 - i0;
     for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
       uint2 r = P.witem[i0 + k];
+      const bool mine = !P.route || P.route[i0 + k] == V_PROBE;
+      if (!mine) r.y = r.x;
       if (MODE == M_LIST_WRITE) {
         const uint32_t e = P.wedge[i0 + k];
         const uint64_t a = P.toff[e], b = P.toff[e + 1];
@@ -528,7 +507,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       cur[k] = r.x;
       endp[k] = r.y;
       nextv[k] = r.x < r.y ? P.adj[r.x] : NONE;
-      ih[k] = 0;
+      ih[k] = mine ? 0u : NONE;  // NONE: the item belongs to another route
     }
     const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
@@ -585,6 +564,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       uint32_t th = 0;
       for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
         const uint32_t hk = ih[k];
+        if (hk == NONE) continue;
         th += hk;
         if (MODE == M_VERTEX && hk) atomicAdd((unsigned long long*)&P.tv[P.wvert[i0 + k]], (unsigned long long)hk);
         if (MODE == M_LIST_COUNT) P.tcnt[P.wedge[i0 + k]] = hk;
@@ -769,6 +749,8 @@ static KParams base_params(aot_graph* g) {
   P.cursor = 0;
   P.cap = 0;
   P.dev = g->dev;
+  P.route = g->routed ? g->route : nullptr;
+  P.rprobe = g->routed ? g->rprobe : nullptr;
   return P;
 }
 
@@ -780,9 +762,20 @@ static aot_status reset_scalars(aot_graph* g, cudaStream_t s) {
 
 static aot_status check_route(aot_graph* g, aot_route route) {
   if (!g) return AOT_ERR_INVALID_ARG;
-  if (route != AOT_ROUTE_PLAIN && route != AOT_ROUTE_PROBE) return AOT_ERR_NOT_READY;
+  if ((int)route < (int)AOT_ROUTE_PLAIN || (int)route > (int)AOT_ROUTE_RANDOM) return AOT_ERR_INVALID_ARG;
+  if (route == AOT_ROUTE_LEARNED && !g->model) return AOT_ERR_NOT_READY;
   if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
   return AOT_OK;
+}
+
+// route the items, then run the pivot kernels and the staging-free kernel
+template <int MODE>
+static aot_status run_mode(aot_graph* g, aot_route route, KParams P, cudaStream_t s) {
+  AOT_TRY(route_items(g, route, s));
+  P.route = g->routed ? g->route : nullptr;
+  P.rprobe = g->routed ? g->rprobe : nullptr;
+  AOT_TRY(launch_bins<MODE>(g, P, s));
+  return launch_ep<MODE>(g, P, s);
 }
 
 __global__ void k_gather_counts(const uint64_t* __restrict__ tv, const int32_t* __restrict__ rank,
@@ -800,7 +793,7 @@ extern "C" aot_status aot_count(aot_graph* g, aot_route route, uint64_t* h_total
   if (!h_total) return AOT_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   AOT_TRY(reset_scalars(g, s));
-  if (g->m > 0) AOT_TRY(launch_bins<M_COUNT>(g, base_params(g), s));
+  if (g->m > 0) AOT_TRY(run_mode<M_COUNT>(g, route, base_params(g), s));
   unsigned long long t = 0;
   AOT_CUDA(cudaMemcpyAsync(&t, &g->dev->total, sizeof(t), cudaMemcpyDeviceToHost, s));
   AOT_CUDA(cudaStreamSynchronize(s));
@@ -817,7 +810,7 @@ extern "C" aot_status aot_count_per_vertex(aot_graph* g, aot_route route, uint64
   AOT_TRY(reset_scalars(g, s));
   if (g->n > 0) {
     AOT_CUDA(cudaMemsetAsync(g->tv, 0, sizeof(uint64_t) * g->n, s));
-    if (g->m > 0) AOT_TRY(launch_bins<M_VERTEX>(g, base_params(g), s));
+    if (g->m > 0) AOT_TRY(run_mode<M_VERTEX>(g, route, base_params(g), s));
     AOT_KERNEL("k_gather_counts", s)
       k_gather_counts<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(g->tv, g->rank, g->n, d_counts);
     AOT_TRY(last_launch());
@@ -843,7 +836,7 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
     if (g->m > 0) {
       AOT_TRY(reset_scalars(g, s));
       AOT_CUDA(cudaMemsetAsync(g->tcnt, 0, sizeof(uint32_t) * g->m, s));
-      AOT_TRY(launch_bins<M_LIST_COUNT>(g, base_params(g), s));
+      AOT_TRY(run_mode<M_LIST_COUNT>(g, route, base_params(g), s));
       AOT_TRY(scan_u32_u64(g->tcnt, g->toff, g->m, g->scan_tmp, s));
       unsigned long long t = 0;
       AOT_CUDA(cudaMemcpyAsync(&t, g->toff + g->m, sizeof(t), cudaMemcpyDeviceToHost, s));
@@ -862,7 +855,7 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
     P.cursor = cursor;
     P.cap = k;
     AOT_TRY(reset_scalars(g, s));
-    AOT_TRY(launch_bins<M_LIST_WRITE>(g, P, s));
+    AOT_TRY(run_mode<M_LIST_WRITE>(g, route, P, s));
     AOT_CUDA(cudaStreamSynchronize(s));
     AOT_TRY(read_device_error(g, s));
   }

@@ -161,6 +161,11 @@ struct aot_graph {
   uint64_t* tv = nullptr;          // n : per-vertex counts (rank space)
   uint32_t* tcnt = nullptr;        // m : triangles per oriented edge (list)
   uint64_t* toff = nullptr;        // m+1
+  uint8_t* route = nullptr;        // m : variant per item (routed runs)
+  uint32_t* rprobe = nullptr;      // n : probe items per pivot (routed runs)
+  uint2* eplist = nullptr;         // m : (item, pivot) of staging-free items
+  bool routed = false;             // route/rprobe/eplist valid for the current run
+  const void* model = nullptr;     // learned router parameters (device)
   void* scan_tmp = nullptr;
   aot::DevScalars* dev = nullptr;
   bool has_list = false;
@@ -174,6 +179,8 @@ struct aot_graph {
 };
 
 namespace aot {
+enum Variant { V_PROBE = 0, V_MERGE = 1, V_BSEARCH = 2 };
+aot_status learned_routes(aot_graph* g, cudaStream_t s);
 aot_status bin_pivots(aot_graph* g, cudaStream_t s);
 aot_status read_device_error(aot_graph* g, cudaStream_t s);
 }  // namespace aot

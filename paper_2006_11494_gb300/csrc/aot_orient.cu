@@ -297,6 +297,7 @@ struct OrientLayout {
   uint32_t* hubinfo;
   uint64_t* tv;
   uint32_t* tcnt; uint64_t* toff;
+  uint8_t* route; uint32_t* rprobe; uint2* eplist;
   void* tmp;
   size_t bytes;
 };
@@ -333,6 +334,9 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
     L.tcnt = c.take<uint32_t>(Es);
     L.toff = c.take<uint64_t>(Es + 1);
   }
+  L.route = c.take<uint8_t>(Es);
+  L.rprobe = c.take<uint32_t>(ns);
+  L.eplist = c.take<uint2>(Es);
   int64_t big = Es > ns ? Es : ns;  // the eta sort and the pivot scans run over n
   size_t tb = radix_tmp_bytes(big);
   size_t sb = scan_tmp_bytes(big + 1);
@@ -384,6 +388,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   g->hub_bitmap = L.hub_bitmap; g->hubinfo = L.hubinfo; g->tv = L.tv;
   g->tcnt = L.tcnt; g->toff = L.toff; g->has_list = !(flags & AOT_FLAG_NO_LIST);
   g->scan_tmp = L.tmp;
+  g->route = L.route; g->rprobe = L.rprobe; g->eplist = L.eplist;
   g->adj = L.adj;
   auto fail = [&](aot_status st) { delete g; return st; };
 

@@ -33,9 +33,30 @@ def check_full(n, s, d, flags=0, order=oracle.ORDER_DESC, listing=True, tuning=N
     if listing:
         lst = g.list(chunk=chunk).cpu().numpy()
         assert np.array_equal(lst, ref.list_canonical(order))
-    for r in (aot.ROUTE_PROBE,):
-        assert g.count(r) == T_ref
+    for r in (aot.ROUTE_PROBE, aot.ROUTE_MERGE, aot.ROUTE_BSEARCH, aot.ROUTE_RANDOM):
+        assert g.count(r) == T_ref, r
     return g, ref
+
+
+ROUTES = ["PLAIN", "PROBE", "MERGE", "BSEARCH", "RANDOM"]
+
+
+def check_routes(n, s, d, tuning=None):
+    """Every route gives the same count, per-vertex counts and canonical list."""
+    import paper_2006_11494_gb300 as aot
+    ref = oracle.Graph(n, s, d)
+    T_ref, t_ref = ref.count_per_vertex()
+    lst_ref = ref.list_canonical()
+    for name in ROUTES:
+        r = getattr(aot, "ROUTE_" + name)
+        g = gpu_graph(n, s, d)
+        if tuning:
+            g.set_tuning(**tuning)
+        assert g.count(r) == T_ref, name
+        T, t = g.count_per_vertex(r)
+        assert T == T_ref and np.array_equal(u64(t), t_ref), name
+        lst = g.list(r, chunk=max(1, len(lst_ref) // 3 + 1)).cpu().numpy()
+        assert np.array_equal(lst, lst_ref), name
 
 
 # ------------------------------------------------------------ closed forms
@@ -100,6 +121,28 @@ def test_chunglu_full_parity():
 def test_every_bin_gives_the_same_answer(tuning):
     n, s, d = gg.rmat_cfg(13, 7)
     check_full(n, s, d, tuning=tuning)
+
+
+@pytest.mark.parametrize("case", ["rmat12", "er", "wheel", "k40", "chunglu"])
+def test_routes_are_invisible_in_the_output(case):
+    if case == "rmat12":
+        n, s, d = gg.rmat_cfg(12, 21)
+    elif case == "er":
+        n = 3000
+        s, d = gg.er(n, 40000, seed=4)
+    elif case == "wheel":
+        n, s, d = gg.wheel(5000)
+    elif case == "k40":
+        n, s, d = gg.complete(40)
+    else:
+        n = 1 << 12
+        s, d = gg.chunglu(n, 2.1, 20.0, seed=8)
+    check_routes(n, s, d)
+
+
+def test_routes_with_every_bin():
+    n, s, d = gg.rmat_cfg(12, 22)
+    check_routes(n, s, d, tuning=dict(warp_max_outdeg=16, cta_max_outdeg=128, seg_bits=2048))
 
 
 def test_asc_order_orientation_and_parity():
