@@ -180,6 +180,62 @@ aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t);
  * not exceed the value the workspace was sized for (32). */
 aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t s);
 
+/* ---- learned router (the build's addition; the paper has no learned part) ----
+ * An 8 -> 64 -> 64 -> 3 perceptron (ReLU hidden layers) predicts, per work
+ * item, the standardised log cost of the three variants (probe, merge, binary
+ * search) from eight features of its oriented edge <u,v> (rank space, u < v):
+ * log1p deg+(u), log1p deg+(v), log1p |{w in N+(u): w > v}|, log1p deg-(u),
+ * log1p deg-(v), log1p deg(u), log1p deg(v), (v - u) / n.  AOT_ROUTE_LEARNED
+ * keeps the probe of Algorithm 3 unless another variant's predicted cost is
+ * lower by more than the model's margin.  Routing never changes results.
+ *
+ * Model buffer (AOT_MLP_MODEL_BYTES, device memory, 16-byte aligned):
+ *   float in_mean[8], in_std[8]    feature standardisation  (bytes   0.. 63)
+ *   float out_mean[4], out_std[4]  output de-standardisation (bytes 64.. 95)
+ *   float margin, reserved[7]                                (bytes 96..127)
+ *   bfloat16 params[4931] from byte 128: W1[64][8], b1[64], W2[64][64],
+ *   b2[64], W3[3][64], b3[3] (row-major [out][in]).
+ * Numerics: bf16 inputs, parameters and hidden activations (round to nearest
+ * even), fp32 accumulation, fp32 outputs. */
+#define AOT_MLP_PARAMS 4931
+#define AOT_MLP_MODEL_BYTES 10240
+
+/* Attach (or detach with NULL) router parameters used by AOT_ROUTE_LEARNED.
+ * The buffer stays owned by the caller and must outlive its use. */
+aot_status aot_graph_set_router(aot_graph* g, const void* d_model);
+
+/* The eight raw (unstandardised) features of every oriented edge, written to
+ * d_feat[m][8] (float, rows in out-CSR edge order).  Ordered on s. */
+aot_status aot_graph_features(aot_graph* g, float* d_feat, aot_stream_t s);
+
+/* Timing capture: run the work items through one variant (0 probe, 1 merge,
+ * 2 binary search) with per-item clock64 timing and write the cycles of each
+ * oriented edge (its walk plus its share of index staging) to d_cycles[m]
+ * (CSR edge order; 0 for items not run).  The probe variant runs every item;
+ * the other two only the items whose hash has its low sample_log2 bits zero
+ * (sample_log2 = 0: all).  These are the router's training labels.
+ * Synchronises s. */
+aot_status aot_graph_record_costs(aot_graph* g, int32_t variant, int32_t sample_log2,
+                                  uint32_t* d_cycles, aot_stream_t s);
+
+/* Network output y[n][3] (standardised log costs) for raw features x[n][8]
+ * (the kernel standardises them with the model's in_mean / in_std).  Uses the
+ * tensor-core inference kernel.  Ordered on s. */
+aot_status aot_mlp_forward(const void* d_model, const float* d_x, int64_t n, float* d_y, aot_stream_t s);
+
+/* Workspace of aot_mlp_train_step for a batch size. */
+aot_status aot_mlp_train_workspace_size(int32_t batch, size_t* bytes);
+
+/* One training step on a batch: forward, loss sum (y - t)^2 / batch with
+ * standardised targets d_t[batch][3], backward; if lr > 0 one Adam step
+ * (beta 0.9 / 0.999, eps 1e-8; step counts from 1) of the fp32 master copy
+ * d_master[4931] with moments d_m1, d_m2, whose bf16 rounding is written back
+ * into the model.  d_grad_out (optional, 4931 floats) receives the gradient
+ * in parameter order; h_loss (optional) the loss (then s is synchronised). */
+aot_status aot_mlp_train_step(void* d_model, float* d_master, float* d_m1, float* d_m2, int32_t step,
+                              float lr, const float* d_x, const float* d_t, int32_t batch, void* d_ws,
+                              size_t ws_bytes, float* d_grad_out, float* h_loss, aot_stream_t s);
+
 /* ---- launch accounting and profiling (no effect on results) ---- */
 
 /* Number of kernels this library has launched in this process. */

@@ -51,6 +51,13 @@ SIGNATURES = {
     "aot_graph_set_tuning": (ctypes.c_int, [P, P, P]),
     "aot_graph_destroy": (ctypes.c_int, [P]),
     "aot_count_per_vertex_static": (ctypes.c_int, [P, P, I64, I32, P, ctypes.POINTER(U64), P]),
+    "aot_graph_set_router": (ctypes.c_int, [P, P]),
+    "aot_graph_features": (ctypes.c_int, [P, P, P]),
+    "aot_graph_record_costs": (ctypes.c_int, [P, I32, I32, P, P]),
+    "aot_mlp_forward": (ctypes.c_int, [P, P, I64, P, P]),
+    "aot_mlp_train_workspace_size": (ctypes.c_int, [I32, ctypes.POINTER(SZ)]),
+    "aot_mlp_train_step": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, I32, P, SZ, P,
+                                          ctypes.POINTER(ctypes.c_float), P]),
     "aot_kernel_launches": (ctypes.c_ulonglong, []),
     "aot_profile_begin": (ctypes.c_int, []),
     "aot_profile_end": (ctypes.c_int, [P, I32, ctypes.POINTER(I32)]),
@@ -198,6 +205,47 @@ def aot_graph_get_tuning(handle: int) -> Tuning:
 def aot_graph_set_tuning(handle: int, tuning: Tuning, stream=None):
     _check(lib().aot_graph_set_tuning(handle, ctypes.byref(tuning), _stream(stream)),
            "aot_graph_set_tuning")
+
+
+MLP_PARAMS = 4931
+MLP_MODEL_BYTES = 10240
+VARIANTS = ("probe", "merge", "bsearch")
+
+
+def aot_graph_set_router(handle: int, model):
+    _check(lib().aot_graph_set_router(handle, _ptr(model) if model is not None else None),
+           "aot_graph_set_router")
+
+
+def aot_graph_features(handle: int, feat, stream=None):
+    _check(lib().aot_graph_features(handle, _ptr(feat), _stream(stream)), "aot_graph_features")
+
+
+def aot_graph_record_costs(handle: int, variant: int, cycles, sample_log2: int = 0, stream=None):
+    _check(lib().aot_graph_record_costs(handle, variant, sample_log2, _ptr(cycles), _stream(stream)),
+           "aot_graph_record_costs")
+
+
+def aot_mlp_forward(model, x, y, stream=None):
+    _check(lib().aot_mlp_forward(_ptr(model), _ptr(x), x.shape[0], _ptr(y), _stream(stream)),
+           "aot_mlp_forward")
+
+
+def aot_mlp_train_workspace_size(batch: int) -> int:
+    b = SZ(0)
+    _check(lib().aot_mlp_train_workspace_size(batch, ctypes.byref(b)), "aot_mlp_train_workspace_size")
+    return b.value
+
+
+def aot_mlp_train_step(model, master, m1, m2, step: int, lr: float, x, t, workspace,
+                       grad_out=None, want_loss: bool = True, stream=None):
+    loss = ctypes.c_float(0.0)
+    _check(lib().aot_mlp_train_step(_ptr(model), _ptr(master), _ptr(m1), _ptr(m2), step, lr,
+                                    _ptr(x), _ptr(t), x.shape[0], _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _ptr(grad_out),
+                                    ctypes.byref(loss) if want_loss else None, _stream(stream)),
+           "aot_mlp_train_step")
+    return loss.value if want_loss else None
 
 
 STATIC_SCRATCH_BYTES = 32 * 1024 * 1024

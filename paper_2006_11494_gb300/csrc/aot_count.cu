@@ -54,7 +54,8 @@ constexpr uint32_t LONG_ITEM = 64;  // items at least this long are walked by th
 // over the exclusive prefix of the lengths.  Returns this lane's hit count.
 template <int MODE, class Probe, class OnW>
 __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uint32_t c,
-                                               uint32_t ie, Probe probe, OnW on_w) {
+                                               uint32_t ie, Probe probe, OnW on_w,
+                                               uint32_t stage_share = 0) {
   const unsigned lane = lane_id();
   const uint32_t it = c + lane;
   const bool has = it < ie && (!P.route || P.route[it] == V_PROBE);
@@ -71,12 +72,14 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
   uint32_t len = r.y - r.x;
   uint32_t ihits = 0;  // hits of the item held by this lane
   uint32_t my = 0;     // hits found by this lane
+  uint32_t mycyc = 0;  // M_TIMED: cycles of the item held by this lane
 
   // ---- long items: the whole warp, 4 x 32 entries per step
   unsigned longm = __ballot_sync(FULL, len >= LONG_ITEM);
   while (longm) {
     const int j = __ffs(longm) - 1;
     longm &= longm - 1;
+    const long long t0 = MODE == M_TIMED ? clock64() : 0;
     const uint32_t x = __shfl_sync(FULL, r.x, j), y = __shfl_sync(FULL, r.y, j);
     uint32_t vj = 0;
     uint64_t tb = 0;
@@ -107,11 +110,15 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
         h += (uint32_t)__popc(hm);
       }
     }
-    if ((int)lane == j) ihits = h;
+    if ((int)lane == j) {
+      ihits = h;
+      if (MODE == M_TIMED) mycyc = sat_cycles(clock64() - t0);
+    }
   }
   if (len >= LONG_ITEM) len = 0;
 
   // ---- short items: flattened
+  const long long ts0 = MODE == M_TIMED ? clock64() : 0;
   const uint32_t incl = warp_inclusive_scan(len);
   const uint32_t total = __shfl_sync(FULL, incl, 31);
   const uint32_t excl = incl - len;
@@ -154,6 +161,12 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
   }
   if (MODE == M_VERTEX && has && ihits) atomicAdd((unsigned long long*)&P.tv[vert], (unsigned long long)ihits);
   if (MODE == M_LIST_COUNT && has) P.tcnt[edge] = ihits;
+  if (MODE == M_TIMED) {
+    // a short item gets the flattened phase's time in proportion to its length
+    const long long tshort = clock64() - ts0;
+    if (has && len > 0 && total > 0) mycyc = sat_cycles((long long)((double)tshort * len / total));
+    if (has) P.cyc[edge] = mycyc + stage_share;
+  }
   return my;
 }
 
@@ -175,6 +188,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
     const uint32_t p = P.pivots[idx];
     if (P.rprobe && P.rprobe[p] == 0) continue;  // every item of p takes another route
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
+    const long long tst0 = MODE == M_TIMED ? clock64() : 0;
     uint32_t ts = 32;
     while (ts < 2 * d) ts <<= 1;
     const uint32_t mask = ts - 1;
@@ -188,6 +202,8 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
       while (atomicCAS(&tab[s], EMPTY, w) != EMPTY) s = (s + 1) & mask;
     }
     __syncwarp();
+    const uint32_t stage_share = MODE == M_TIMED
+        ? sat_cycles((clock64() - tst0) / (long long)max(1u, P.wofs[p + 1] - P.wofs[p])) : 0u;
     auto probe = [&](uint32_t w, uint32_t& slot) -> bool {
       uint32_t s = hash_slot(w, mask);
       while (true) {
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
     auto on_w = [&](uint32_t, uint32_t slot) { atomicAdd(&cnt[slot], 1u); };
     const uint32_t ib = P.wofs[p], ie = P.wofs[p + 1];
     uint32_t ph = 0;
-    for (uint32_t c = ib; c < ie; c += 32) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w);
+    for (uint32_t c = ib; c < ie; c += 32) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w, stage_share);
     if (MODE == M_VERTEX) {
       __syncwarp();
       for (uint32_t i = lane; i < ts; i += 32)
@@ -239,6 +255,7 @@ __global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_m
       continue;
     }
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
+    const long long tst0 = MODE == M_TIMED ? clock64() : 0;
     uint32_t ts = 64;
     while (ts < 2 * d) ts <<= 1;
     const uint32_t mask = ts - 1;
@@ -252,6 +269,9 @@ __global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_m
       while (atomicCAS(&tab[s], EMPTY, w) != EMPTY) s = (s + 1) & mask;
     }
     __syncthreads();
+    // the block's staging time, spread over the pivot's items (all warps waited for it)
+    const uint32_t stage_share = MODE == M_TIMED
+        ? sat_cycles((clock64() - tst0) * (long long)nw / (long long)max(1u, P.wofs[p + 1] - P.wofs[p])) : 0u;
     auto probe = [&](uint32_t w, uint32_t& slot) -> bool {
       uint32_t s = hash_slot(w, mask);
       while (true) {
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_m
     auto on_w = [&](uint32_t, uint32_t slot) { atomicAdd(&cnt[slot], 1u); };
     const uint32_t ib = P.wofs[p], ie = P.wofs[p + 1];
     uint32_t ph = 0;
-    for (uint32_t c = ib + 32 * wid; c < ie; c += 32 * nw) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w);
+    for (uint32_t c = ib + 32 * wid; c < ie; c += 32 * nw) ph += walk_chunk<MODE>(P, p, c, ie, probe, on_w, stage_share);
     found += ph;
     if (MODE == M_VERTEX) {
       uint32_t tot = warp_sum(ph);
@@ -458,7 +478,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
   uint32_t* nextv = endp + SEG_ITEMS;
   uint32_t* ih = nextv + SEG_ITEMS;
   __shared__ uint32_t s_task, s_hub, s_pe, s_next;
-  __shared__ unsigned long long s_hits;
+  __shared__ unsigned long long s_hits, s_stage;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
   const uint32_t ntasks = task_ofs[nh];
   for (uint32_t i = threadIdx.x; i < seg_words; i += blockDim.x) bm[i] = 0;
@@ -467,6 +487,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     if (threadIdx.x == 0) {
       s_task = atomicAdd(&P.dev->counters[Q_SEG], 1u);
       s_hits = 0;
+      s_stage = 0;
     }
     __syncthreads();
     const uint32_t task = s_task;
@@ -523,11 +544,13 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       __syncthreads();
       const uint32_t pe = s_pe;
       if (pe > pc) {
+        const long long tset0 = MODE == M_TIMED ? clock64() : 0;
         for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
           const uint32_t b = P.adj[k] - segLo;
           atomicOr(&bm[b >> 5], 1u << (b & 31));
         }
         __syncthreads();
+        if (MODE == M_TIMED && threadIdx.x == 0) s_stage += (unsigned long long)(clock64() - tset0) * (blockDim.x >> 5);
         while (true) {
           uint32_t k = 0;
           if (lane == 0) k = atomicAdd(&s_next, 1u);
@@ -542,7 +565,9 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
             vj = P.wvert[i0 + k];
             tb = P.toff[P.wedge[i0 + k]];
           }
+          const long long tv0 = MODE == M_TIMED ? clock64() : 0;
           seg_walk_item<MODE>(P, bm, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+          if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
           __syncwarp();
           if (lane == 0) {
             cur[k] = x;
@@ -560,7 +585,13 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       pc = pe;
       __syncthreads();
     }
-    if (MODE != M_COUNT) {
+    if (MODE == M_TIMED) {
+      const unsigned long long sh = s_stage / (unsigned long long)max(1u, nk);
+      const uint32_t share = sh > 0xffffffffull ? 0xffffffffu : (uint32_t)sh;
+      for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x)
+        if (ih[k] != NONE) P.cyc[P.wedge[i0 + k]] = ih[k] + share;
+    }
+    if (MODE != M_COUNT && MODE != M_TIMED) {
       uint32_t th = 0;
       for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
         const uint32_t hk = ih[k];
@@ -595,11 +626,11 @@ __global__ void k_hub_info(const uint32_t* __restrict__ pivots, uint32_t nh,
 }
 
 // ------------------------------------------------------------------ driver
-#define AOT_MODE_NAMES(k) {#k "/count", #k "/vertex", #k "/list_count", #k "/list_write"}
-static const char* const kWarpNames[4] = AOT_MODE_NAMES(k_warp_pivots);
-static const char* const kCtaNames[4] = AOT_MODE_NAMES(k_cta_pivots);
-static const char* const kHubNames[4] = AOT_MODE_NAMES(k_hub_walk);
-static const char* const kSegNames[4] = AOT_MODE_NAMES(k_seg_pivots);
+#define AOT_MODE_NAMES(k) {#k "/count", #k "/vertex", #k "/list_count", #k "/list_write", #k "/timed"}
+static const char* const kWarpNames[5] = AOT_MODE_NAMES(k_warp_pivots);
+static const char* const kCtaNames[5] = AOT_MODE_NAMES(k_cta_pivots);
+static const char* const kHubNames[5] = AOT_MODE_NAMES(k_hub_walk);
+static const char* const kSegNames[5] = AOT_MODE_NAMES(k_seg_pivots);
 template <int MODE>
 static const char* mode_name(const char* base) {
   if (base[2] == 'w') return kWarpNames[MODE];
@@ -641,7 +672,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     uint32_t ts_max = 64;
     while (ts_max < 2 * g->binned_cta_max) ts_max <<= 1;
     size_t smem = (size_t)ts_max * 2 * sizeof(uint32_t);
-    static size_t attr_done[4] = {0, 0, 0, 0};
+    static size_t attr_done[5] = {0, 0, 0, 0, 0};
     if (attr_done[MODE] < smem) {
       AOT_CUDA(cudaFuncSetAttribute(k_cta_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr_done[MODE] = smem;
@@ -666,7 +697,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_TRY(scan_u32_u32(cnt, task_ofs, nh, g->scan_tmp, s));
     const uint32_t seg_bits = g->tune.seg_bits;
     const size_t seg_smem = seg_smem_bytes(seg_bits);
-    static bool seg_attr[4] = {false, false, false, false};
+    static bool seg_attr[5] = {false, false, false, false, false};
     if (!seg_attr[MODE]) {
       AOT_CUDA(cudaFuncSetAttribute(k_seg_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)seg_smem_bytes(SEG_BITS_MAX)));
@@ -751,6 +782,7 @@ static KParams base_params(aot_graph* g) {
   P.dev = g->dev;
   P.route = g->routed ? g->route : nullptr;
   P.rprobe = g->routed ? g->rprobe : nullptr;
+  P.cyc = nullptr;
   return P;
 }
 
@@ -770,8 +802,9 @@ static aot_status check_route(aot_graph* g, aot_route route) {
 
 // route the items, then run the pivot kernels and the staging-free kernel
 template <int MODE>
-static aot_status run_mode(aot_graph* g, aot_route route, KParams P, cudaStream_t s) {
-  AOT_TRY(route_items(g, route, s));
+static aot_status run_mode(aot_graph* g, aot_route route, KParams P, cudaStream_t s,
+                           int sample_log2 = 0) {
+  AOT_TRY(route_items(g, route, s, sample_log2));
   P.route = g->routed ? g->route : nullptr;
   P.rprobe = g->routed ? g->rprobe : nullptr;
   AOT_TRY(launch_bins<MODE>(g, P, s));
@@ -823,6 +856,23 @@ extern "C" aot_status aot_count_per_vertex(aot_graph* g, aot_route route, uint64
     *h_total = t;
   }
   return AOT_OK;
+}
+
+extern "C" aot_status aot_graph_record_costs(aot_graph* g, int32_t variant, int32_t sample_log2,
+                                             uint32_t* d_cycles, aot_stream_t stream) {
+  if (!g || (g->m > 0 && !d_cycles) || variant < 0 || variant > 2) return AOT_ERR_INVALID_ARG;
+  if (sample_log2 < 0 || sample_log2 > 30) return AOT_ERR_INVALID_ARG;
+  if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (g->m == 0) return AOT_OK;
+  AOT_CUDA(cudaMemsetAsync(d_cycles, 0, sizeof(uint32_t) * g->m, s));
+  AOT_TRY(reset_scalars(g, s));
+  const aot_route r = variant == V_PROBE ? AOT_ROUTE_PROBE : variant == V_MERGE ? AOT_ROUTE_MERGE : AOT_ROUTE_BSEARCH;
+  KParams P = base_params(g);
+  P.cyc = d_cycles;
+  AOT_TRY(run_mode<M_TIMED>(g, r, P, s, variant == V_PROBE ? 0 : sample_log2));
+  AOT_CUDA(cudaStreamSynchronize(s));
+  return read_device_error(g, s);
 }
 
 extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_out,

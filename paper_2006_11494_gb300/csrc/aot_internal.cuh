@@ -144,6 +144,7 @@ struct aot_graph {
   // rank-space arrays in the workspace
   int32_t* perm = nullptr;   // n : eta position -> original id
   int32_t* rank = nullptr;   // n : original id -> eta position
+  uint32_t* degr = nullptr;  // n : undirected degree per eta position
   uint32_t* off = nullptr;   // n+1
   uint32_t* adj = nullptr;   // m
   uint32_t* outdeg = nullptr;  // n
@@ -179,7 +180,7 @@ struct aot_graph {
 };
 
 namespace aot {
-enum Variant { V_PROBE = 0, V_MERGE = 1, V_BSEARCH = 2 };
+enum Variant { V_PROBE = 0, V_MERGE = 1, V_BSEARCH = 2, V_SKIP = 3 };
 aot_status learned_routes(aot_graph* g, cudaStream_t s);
 aot_status bin_pivots(aot_graph* g, cudaStream_t s);
 aot_status read_device_error(aot_graph* g, cudaStream_t s);

@@ -5,7 +5,8 @@
 
 namespace aot {
 
-enum Mode { M_COUNT = 0, M_VERTEX = 1, M_LIST_COUNT = 2, M_LIST_WRITE = 3 };
+// M_TIMED counts like M_COUNT and also records per-edge cycles into cyc[]
+enum Mode { M_COUNT = 0, M_VERTEX = 1, M_LIST_COUNT = 2, M_LIST_WRITE = 3, M_TIMED = 4 };
 enum Queue { Q_WARP = 1, Q_CTA = 2, Q_HUB = 3, Q_SEG = 4, Q_EPLIST = 5 };
 
 struct KParams {
@@ -25,6 +26,7 @@ struct KParams {
   uint64_t cursor, cap;    // listing window [cursor, cursor + cap)
   DevScalars* dev;
   const uint8_t* route;    // variant per item (nullptr: every item probes)
+  uint32_t* cyc;           // M_TIMED: cycles per oriented edge
   const uint32_t* rprobe;  // probe items per pivot (nullptr: all items)
 };
 
@@ -40,8 +42,12 @@ __device__ __forceinline__ void emit(const KParams& P, uint64_t idx, uint32_t p,
   }
 }
 
+__device__ __forceinline__ uint32_t sat_cycles(long long c) {
+  return c <= 0 ? 0u : (c >= 0xffffffffll ? 0xffffffffu : (uint32_t)c);
+}
+
 template <int MODE>
 aot_status launch_ep(aot_graph* g, const KParams& P, cudaStream_t s);
-aot_status route_items(aot_graph* g, aot_route route, cudaStream_t s);
+aot_status route_items(aot_graph* g, aot_route route, cudaStream_t s, int sample_log2 = 0);
 
 }  // namespace aot

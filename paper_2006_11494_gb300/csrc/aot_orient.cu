@@ -71,12 +71,14 @@ __global__ void k_eta_keys(const uint32_t* __restrict__ deg, int32_t n, int bits
 }
 
 __global__ void k_rank_from_perm(const uint32_t* __restrict__ perm_sorted, int32_t n,
-                                 int32_t* __restrict__ perm, int32_t* __restrict__ rank) {
+                                 const uint32_t* __restrict__ deg, int32_t* __restrict__ perm,
+                                 int32_t* __restrict__ rank, uint32_t* __restrict__ degr) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   uint32_t v = perm_sorted[r];
   perm[r] = (int32_t)v;
   rank[v] = (int32_t)r;
+  degr[r] = deg[v];
 }
 
 __global__ void k_relabel(const uint64_t* __restrict__ ukeys, int64_t m, int bits,
@@ -289,7 +291,7 @@ struct OrientLayout {
   uint32_t* pos;
   uint32_t* deg;
   uint32_t* ek0; uint32_t* ek1; uint32_t* ev0; uint32_t* ev1;
-  int32_t* perm; int32_t* rank;
+  int32_t* perm; int32_t* rank; uint32_t* degr;
   uint32_t* off; uint32_t* adj; uint32_t* outdeg;
   uint32_t* wofs; uint32_t* items; uint64_t* walk;
   uint32_t* bin_pivots; uint32_t* bin_flag; uint32_t* bin_pos;
@@ -315,7 +317,7 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
   L.deg = c.take<uint32_t>(ns);
   L.ek0 = c.take<uint32_t>(ns); L.ek1 = c.take<uint32_t>(ns);
   L.ev0 = c.take<uint32_t>(ns); L.ev1 = c.take<uint32_t>(ns);
-  L.perm = c.take<int32_t>(ns); L.rank = c.take<int32_t>(ns);
+  L.perm = c.take<int32_t>(ns); L.rank = c.take<int32_t>(ns); L.degr = c.take<uint32_t>(ns);
   L.off = c.take<uint32_t>(ns + 1);
   L.adj = c.take<uint32_t>(Es + 4);  // padded: 128-bit loads may read up to 3 entries past m
   L.outdeg = c.take<uint32_t>(ns);
@@ -382,7 +384,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   g->flags = flags;
   g->bits = num_vertices > 1 ? ceil_log2((uint64_t)num_vertices) : 1;
   g->dev = L.dev;
-  g->perm = L.perm; g->rank = L.rank; g->off = L.off; g->outdeg = L.outdeg;
+  g->perm = L.perm; g->rank = L.rank; g->degr = L.degr; g->off = L.off; g->outdeg = L.outdeg;
   g->wofs = L.wofs; g->items = L.items; g->walk = L.walk;
   g->bin_pivots = L.bin_pivots; g->bin_flag = L.bin_flag; g->bin_pos = L.bin_pos;
   g->hub_bitmap = L.hub_bitmap; g->hubinfo = L.hubinfo; g->tv = L.tv;
@@ -441,7 +443,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, s, &ko, &vo);
     if (st) return fail(st);
     AOT_KERNEL("k_rank_from_perm", s)
-      k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.perm, L.rank);
+      k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.deg, L.perm, L.rank, L.degr);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   // 3. orient: relabel, sort, split into out-CSR

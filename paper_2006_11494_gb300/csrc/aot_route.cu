@@ -17,17 +17,20 @@
 namespace aot {
 
 // -------------------------------------------------------------- route fill
-__global__ void k_route_fill(uint8_t* __restrict__ route, int64_t m, int variant, uint64_t seed) {
+// variant >= 0: every item takes it (only items whose hash has its low
+// sample_log2 bits zero when sample_log2 > 0; the others are skipped);
+// variant < 0: a random variant per item.  Hash: splitmix64 of (seed, item).
+__global__ void k_route_fill(uint8_t* __restrict__ route, int64_t m, int variant, uint64_t seed,
+                             int sample_log2) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
+  uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
   uint8_t v = (uint8_t)variant;
-  if (variant < 0) {  // random: splitmix64 output of (seed, item) mod 3
-    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    v = (uint8_t)(z % 3);
-  }
+  if (variant < 0) v = (uint8_t)(z % 3);
+  else if (sample_log2 > 0 && (z & ((1ull << sample_log2) - 1)) != 0) v = V_SKIP;
   route[i] = v;
 }
 
@@ -44,7 +47,7 @@ __global__ void k_route_lists(const uint32_t* __restrict__ wofs, int32_t n,
     const uint32_t it = c + lane;
     const bool has = it < e;
     const uint8_t v = has ? route[it] : (uint8_t)V_PROBE;
-    const bool ep = has && v != V_PROBE;
+    const bool ep = has && (v == V_MERGE || v == V_BSEARCH);
     probes += (uint32_t)__popc(__ballot_sync(FULL, has && v == V_PROBE));
     const unsigned em = __ballot_sync(FULL, ep);
     if (em) {
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   uint64_t found = 0;
   for (uint32_t li = gw; li < count; li += nwarps) {
+    const long long t0 = MODE == M_TIMED ? clock64() : 0;
     const uint2 ent = eplist[li];
     const uint32_t it = ent.x, p = ent.y;
     const uint2 r = P.witem[it];
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
     uint32_t vert = 0, edge = 0;
     uint64_t tb = 0;
     if (MODE != M_COUNT) vert = P.wvert[it];
-    if (MODE >= M_LIST_COUNT) edge = P.wedge[it];
+    if (MODE >= M_LIST_COUNT) edge = P.wedge[it];  // list modes and M_TIMED
     if (MODE == M_LIST_WRITE) {
       const uint64_t a = P.toff[edge], b = P.toff[edge + 1];
       if (a == b || b <= P.cursor || a >= P.cursor + P.cap) continue;
@@ -158,16 +162,17 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
         atomicAdd((unsigned long long*)&P.tv[p], (unsigned long long)h);
       }
       if (MODE == M_LIST_COUNT) P.tcnt[edge] = h;
+      if (MODE == M_TIMED) P.cyc[edge] = sat_cycles(clock64() - t0);
     }
   }
   if (lane == 0 && found) atomicAdd(&P.dev->total, (unsigned long long)found);
 }
 
 // ------------------------------------------------------------------ driver
-#define AOT_EP_NAMES {"k_items_ep/count", "k_items_ep/vertex", "k_items_ep/list_count", "k_items_ep/list_write"}
-static const char* const kEpNames[4] = AOT_EP_NAMES;
+#define AOT_EP_NAMES {"k_items_ep/count", "k_items_ep/vertex", "k_items_ep/list_count", "k_items_ep/list_write", "k_items_ep/timed"}
+static const char* const kEpNames[5] = AOT_EP_NAMES;
 
-aot_status route_items(aot_graph* g, aot_route route, cudaStream_t s) {
+aot_status route_items(aot_graph* g, aot_route route, cudaStream_t s, int sample_log2) {
   g->routed = false;
   if (route == AOT_ROUTE_PLAIN || route == AOT_ROUTE_PROBE) return AOT_OK;
   if (g->m == 0) return AOT_OK;
@@ -179,7 +184,7 @@ aot_status route_items(aot_graph* g, aot_route route, cudaStream_t s) {
     const int variant = route == AOT_ROUTE_MERGE ? V_MERGE
                         : route == AOT_ROUTE_BSEARCH ? V_BSEARCH : -1;
     AOT_KERNEL("k_route_fill", s)
-      k_route_fill<<<grid_m, T, 0, s>>>(g->route, g->m, variant, 0x5EED5EEDull);
+      k_route_fill<<<grid_m, T, 0, s>>>(g->route, g->m, variant, 0x5EED5EEDull, sample_log2);
     AOT_TRY(last_launch());
   }
   AOT_CUDA(cudaMemsetAsync(&g->dev->counters[Q_EPLIST], 0, sizeof(unsigned int), s));
@@ -207,5 +212,6 @@ template aot_status launch_ep<M_COUNT>(aot_graph*, const KParams&, cudaStream_t)
 template aot_status launch_ep<M_VERTEX>(aot_graph*, const KParams&, cudaStream_t);
 template aot_status launch_ep<M_LIST_COUNT>(aot_graph*, const KParams&, cudaStream_t);
 template aot_status launch_ep<M_LIST_WRITE>(aot_graph*, const KParams&, cudaStream_t);
+template aot_status launch_ep<M_TIMED>(aot_graph*, const KParams&, cudaStream_t);
 
 }  // namespace aot
