@@ -204,6 +204,10 @@ aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t 
  * The buffer stays owned by the caller and must outlive its use. */
 aot_status aot_graph_set_router(aot_graph* g, const void* d_model);
 
+/* Router that aot_orient attaches to every new graph (process-wide; NULL:
+ * none, the initial state).  Batches use it for AOT_ROUTE_LEARNED. */
+aot_status aot_set_default_router(const void* d_model);
+
 /* The eight raw (unstandardised) features of every oriented edge, written to
  * d_feat[m][8] (float, rows in out-CSR edge order).  Ordered on s. */
 aot_status aot_graph_features(aot_graph* g, float* d_feat, aot_stream_t s);
@@ -285,6 +289,43 @@ aot_status aot_profile_end(aot_profile_entry* out, int32_t cap, int32_t* count);
 aot_status aot_count_per_vertex_static(const int32_t* d_src, const int32_t* d_dst,
                                        int64_t num_edges, int32_t num_vertices,
                                        uint64_t* d_counts, uint64_t* h_total, aot_stream_t s);
+
+/* Tuning that aot_orient gives every new graph (process-wide; the built-in
+ * defaults until set).  Invalid values return AOT_ERR_INVALID_ARG. */
+aot_status aot_set_default_tuning(const aot_tuning* t);
+aot_status aot_get_default_tuning(aot_tuning* t);
+
+/* Autotuner: coordinate search over the bin thresholds (CTA-hash cutoff,
+ * warp cutoff), CTA size and bitmap segment width, timing each candidate on
+ * this graph with CUDA events (best of reps) in mode 0 (count) or 1
+ * (per-vertex count).  The fastest tuning is set on the graph and returned in
+ * *best_out (may be NULL) with its time in *h_best_ms (may be NULL).
+ * Synchronises s.  Results never change, only speed. */
+aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tuning* best_out,
+                    float* h_best_ms, aot_stream_t s);
+
+/* ---- batches of independent graphs ---- */
+
+/* Device workspace for aot_batch (an upper bound for these totals). */
+aot_status aot_batch_workspace_size(int64_t total_edges, int32_t num_graphs, int64_t total_vertices,
+                                    size_t* bytes);
+
+/* Per-graph triangle counts and per-vertex counts of num_graphs independent
+ * graphs in one pass.  Graph g owns the pairs [d_edge_ofs[g], d_edge_ofs[g+1])
+ * of d_src / d_dst, with LOCAL ids in [0, d_nv[g]) (int64 offsets, G+1 of
+ * them, d_edge_ofs[0] = 0, d_edge_ofs[G] = total_edges; total_vertices =
+ * sum of d_nv).  Output: d_tri[g] (uint64) and d_vcount[voff[g] + v] = t(v)
+ * (uint64) with voff the exclusive prefix of d_nv.  The batch is processed as
+ * the disjoint union of its graphs (one orientation, one set of persistent
+ * bin kernels); the counting phase is captured into a CUDA graph and
+ * launched when s is a created stream that is not already capturing (else
+ * its kernels are launched on s directly).  Synchronises s.
+ * Errors: AOT_ERR_INVALID_ARG for inconsistent offsets or counts,
+ * AOT_ERR_VERTEX_RANGE if an id lies outside its own graph. */
+aot_status aot_batch(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
+                     const int32_t* d_nv, int32_t num_graphs, int64_t total_edges,
+                     int64_t total_vertices, aot_route route, uint64_t* d_tri, uint64_t* d_vcount,
+                     void* d_ws, size_t ws_bytes, aot_stream_t s);
 
 /* Free the host handle (the workspace stays with the caller). */
 aot_status aot_graph_destroy(aot_graph* g);

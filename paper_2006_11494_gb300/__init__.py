@@ -58,6 +58,12 @@ SIGNATURES = {
     "aot_mlp_train_workspace_size": (ctypes.c_int, [I32, ctypes.POINTER(SZ)]),
     "aot_mlp_train_step": (ctypes.c_int, [P, P, P, P, I32, ctypes.c_float, P, P, I32, P, SZ, P,
                                           ctypes.POINTER(ctypes.c_float), P]),
+    "aot_set_default_tuning": (ctypes.c_int, [P]),
+    "aot_get_default_tuning": (ctypes.c_int, [P]),
+    "aot_tune": (ctypes.c_int, [P, I32, I32, P, ctypes.POINTER(ctypes.c_float), P]),
+    "aot_set_default_router": (ctypes.c_int, [P]),
+    "aot_batch_workspace_size": (ctypes.c_int, [I64, I32, I64, ctypes.POINTER(SZ)]),
+    "aot_batch": (ctypes.c_int, [P, P, P, P, I32, I64, I64, ctypes.c_int, P, P, P, SZ, P]),
     "aot_kernel_launches": (ctypes.c_ulonglong, []),
     "aot_profile_begin": (ctypes.c_int, []),
     "aot_profile_end": (ctypes.c_int, [P, I32, ctypes.POINTER(I32)]),
@@ -277,6 +283,51 @@ def aot_profile_end() -> dict:
     _check(lib().aot_profile_end(ctypes.cast(arr, P), cap, ctypes.byref(cnt)), "aot_profile_end")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(min(cnt.value, cap))}
+
+
+def aot_set_default_tuning(tuning: Tuning):
+    _check(lib().aot_set_default_tuning(ctypes.byref(tuning)), "aot_set_default_tuning")
+
+
+def aot_get_default_tuning() -> Tuning:
+    t = Tuning()
+    _check(lib().aot_get_default_tuning(ctypes.byref(t)), "aot_get_default_tuning")
+    return t
+
+
+def aot_tune(handle: int, mode: int = 0, reps: int = 2, stream=None):
+    """Autotune the graph's launch tuning in place; returns (Tuning, best ms)."""
+    t = Tuning()
+    ms = ctypes.c_float(0.0)
+    _check(lib().aot_tune(handle, mode, reps, ctypes.byref(t), ctypes.byref(ms), _stream(stream)),
+           "aot_tune")
+    return t, ms.value
+
+
+def aot_set_default_router(model):
+    _check(lib().aot_set_default_router(_ptr(model) if model is not None else None),
+           "aot_set_default_router")
+
+
+def aot_batch_workspace_size(total_edges: int, num_graphs: int, total_vertices: int) -> int:
+    b = SZ(0)
+    _check(lib().aot_batch_workspace_size(total_edges, num_graphs, total_vertices, ctypes.byref(b)),
+           "aot_batch_workspace_size")
+    return b.value
+
+
+def aot_batch(src, dst, edge_ofs, nv, route, tri, vcount, workspace, total_vertices=None,
+              stream=None):
+    """Counts of a batch of graphs (local ids per graph); fills tri[G] and
+    vcount[sum nv] (int64 CUDA tensors holding uint64 counts)."""
+    G = nv.numel()
+    E = src.numel()
+    if total_vertices is None:
+        total_vertices = int(nv.sum().item())
+    _check(lib().aot_batch(_ptr(src), _ptr(dst), _ptr(edge_ofs), _ptr(nv), G, E, total_vertices,
+                           route, _ptr(tri), _ptr(vcount) if total_vertices > 0 else None,
+                           _ptr(workspace), workspace.numel() * workspace.element_size(),
+                           _stream(stream)), "aot_batch")
 
 
 def aot_graph_destroy(handle: int):

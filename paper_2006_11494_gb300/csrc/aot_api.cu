@@ -2,7 +2,61 @@
 // destroy.  The heavy entry points live next to their kernels.
 #include "aot_internal.cuh"
 
+#include <mutex>
+
 using namespace aot;
+
+namespace aot {
+static std::mutex g_default_mu;
+static Tuning g_default_tuning;
+static const void* g_default_router = nullptr;
+const void* default_router() {
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  return g_default_router;
+}
+Tuning default_tuning() {
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  return g_default_tuning;
+}
+static bool tuning_valid(const aot_tuning* t) {
+  return !(t->warp_max_outdeg > 64 || t->cta_max_outdeg > 8192 ||
+           t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
+           (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
+           t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
+           (t->seg_bits & 31));
+}
+}  // namespace aot
+
+extern "C" aot_status aot_set_default_tuning(const aot_tuning* t) {
+  if (!t || !tuning_valid(t)) return AOT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  g_default_tuning.warp_max_outdeg = t->warp_max_outdeg;
+  g_default_tuning.cta_max_outdeg = t->cta_max_outdeg;
+  g_default_tuning.cta_threads = t->cta_threads;
+  g_default_tuning.hub_bitmaps = t->hub_bitmaps;
+  g_default_tuning.hub_mode = t->hub_mode;
+  g_default_tuning.seg_bits = t->seg_bits;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_set_default_router(const void* d_model) {
+  if (d_model && (reinterpret_cast<uintptr_t>(d_model) & 15)) return AOT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  g_default_router = d_model;
+  return AOT_OK;
+}
+
+extern "C" aot_status aot_get_default_tuning(aot_tuning* t) {
+  if (!t) return AOT_ERR_INVALID_ARG;
+  Tuning d = default_tuning();
+  t->warp_max_outdeg = d.warp_max_outdeg;
+  t->cta_max_outdeg = d.cta_max_outdeg;
+  t->cta_threads = d.cta_threads;
+  t->hub_bitmaps = d.hub_bitmaps;
+  t->hub_mode = d.hub_mode;
+  t->seg_bits = d.seg_bits;
+  return AOT_OK;
+}
 
 extern "C" const char* aot_status_string(aot_status st) {
   switch (st) {
@@ -74,13 +128,7 @@ extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
 }
 
 extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, aot_stream_t stream) {
-  if (!g || !t) return AOT_ERR_INVALID_ARG;
-  if (t->warp_max_outdeg > 64 || t->cta_max_outdeg > 8192 ||
-      t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
-      (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
-      t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
-      (t->seg_bits & 31))
-    return AOT_ERR_INVALID_ARG;
+  if (!g || !t || !tuning_valid(t)) return AOT_ERR_INVALID_ARG;
   Tuning old = g->tune;
   g->tune.warp_max_outdeg = t->warp_max_outdeg;
   g->tune.cta_max_outdeg = t->cta_max_outdeg;

@@ -913,3 +913,88 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
   *h_next = cursor + k;
   return AOT_OK;
 }
+
+// ---------------------------------------------------------------- autotuner
+// Coordinate search over the launch tuning of one graph: each candidate is
+// binned and timed (CUDA events, best of reps) on the graph itself in the
+// requested mode; the fastest tuning is kept on the graph and returned.
+namespace aot {
+static aot_status time_mode(aot_graph* g, int mode, int reps, cudaStream_t s, float* ms_out) {
+  cudaEvent_t a, b;
+  AOT_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return AOT_ERR_CUDA;
+  }
+  float best = 3.0e38f;
+  aot_status st = AOT_OK;
+  for (int r = 0; r < reps && st == AOT_OK; ++r) {
+    st = reset_scalars(g, s);
+    if (st == AOT_OK && mode == 1) st = cudaMemsetAsync(g->tv, 0, sizeof(uint64_t) * g->n, s) ? AOT_ERR_CUDA : AOT_OK;
+    if (st != AOT_OK) break;
+    cudaEventRecord(a, s);
+    st = mode == 1 ? run_mode<M_VERTEX>(g, AOT_ROUTE_PLAIN, base_params(g), s)
+                   : run_mode<M_COUNT>(g, AOT_ROUTE_PLAIN, base_params(g), s);
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) st = AOT_ERR_CUDA;
+    float ms = 0.f;
+    if (st == AOT_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_out = best;
+  return st;
+}
+}  // namespace aot
+
+extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tuning* best_out,
+                               float* h_best_ms, aot_stream_t stream) {
+  if (!g || mode < 0 || mode > 1 || reps < 1 || reps > 100) return AOT_ERR_INVALID_ARG;
+  if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  aot_tuning cur;
+  AOT_TRY(aot_graph_get_tuning(g, &cur));
+  float best_ms = 0.f;
+  if (g->m > 0) {
+    AOT_TRY(time_mode(g, mode, reps, s, &best_ms));
+    auto trial = [&](aot_tuning cand) -> aot_status {
+      if (aot_graph_set_tuning(g, &cand, stream) != AOT_OK) return AOT_OK;  // skip invalid candidates
+      float ms = 0.f;
+      AOT_TRY(time_mode(g, mode, reps, s, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        cur = cand;
+      }
+      return AOT_OK;
+    };
+    const uint32_t ctas[] = {64, 256, 512, 1024, 2048, 4096};
+    for (uint32_t c : ctas) {
+      aot_tuning t = cur;
+      t.cta_max_outdeg = c;
+      t.warp_max_outdeg = c < t.warp_max_outdeg ? c : t.warp_max_outdeg;
+      AOT_TRY(trial(t));
+    }
+    const int threads[] = {256, 512, 1024};
+    for (int th : threads) {
+      aot_tuning t = cur;
+      t.cta_threads = th;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t warps[] = {16, 32, 64};
+    for (uint32_t w : warps) {
+      aot_tuning t = cur;
+      t.warp_max_outdeg = w <= t.cta_max_outdeg ? w : t.cta_max_outdeg;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t segs[] = {1572864u, 1048576u};
+    for (uint32_t sb : segs) {
+      aot_tuning t = cur;
+      t.seg_bits = sb;
+      AOT_TRY(trial(t));
+    }
+    AOT_TRY(aot_graph_set_tuning(g, &cur, stream));
+  }
+  if (best_out) *best_out = cur;
+  if (h_best_ms) *h_best_ms = best_ms;
+  return AOT_OK;
+}

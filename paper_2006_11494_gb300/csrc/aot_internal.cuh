@@ -183,5 +183,7 @@ namespace aot {
 enum Variant { V_PROBE = 0, V_MERGE = 1, V_BSEARCH = 2, V_SKIP = 3 };
 aot_status learned_routes(aot_graph* g, cudaStream_t s);
 aot_status bin_pivots(aot_graph* g, cudaStream_t s);
+Tuning default_tuning();
+const void* default_router();
 aot_status read_device_error(aot_graph* g, cudaStream_t s);
 }  // namespace aot

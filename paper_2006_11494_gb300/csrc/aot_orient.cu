@@ -372,13 +372,14 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (num_edges >= (int64_t(1) << 40)) return AOT_ERR_OVERFLOW;
   if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) return AOT_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  Tuning tune;
-  OrientLayout L = carve_orient(d_workspace, num_edges, num_vertices, flags, tune);
+  Tuning tune = default_tuning();
+  OrientLayout L = carve_orient(d_workspace, num_edges, num_vertices, flags, Tuning());
   if (ws_bytes < L.bytes) return AOT_ERR_WORKSPACE;
   if (num_edges > 0 && num_vertices == 0) return AOT_ERR_VERTEX_RANGE;
 
   aot_graph* g = new aot_graph();
   g->tune = tune;
+  g->model = default_router();
   g->n = num_vertices;
   g->num_edges = num_edges;
   g->flags = flags;
