@@ -278,8 +278,8 @@ aot_status aot_profile_end(aot_profile_entry* out, int32_t cap, int32_t* count);
  * Limit: the workspace that aot_orient_workspace_size reports for
  * (num_edges, num_vertices, AOT_FLAG_NO_LIST) must fit the array, else the
  * call returns AOT_ERR_OVERFLOW and does nothing (e.g. 262,144 pairs over
- * 16,384 vertices fit in 10.9 MB; 1,200,000 pairs over 65,536 vertices need
- * 48.9 MB and are rejected).
+ * 16,384 vertices fit in 9.4 MB; 1,200,000 pairs over 65,536 vertices need
+ * 42.0 MB and are rejected).
  * The first call on a device (run with that device current) looks up the
  * array's device address and caches it: make that first call before any
  * stream capture.  All calls share the array, which keeps the last call's

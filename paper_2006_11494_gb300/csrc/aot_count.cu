@@ -516,6 +516,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     const uint32_t i0 = P.wofs[p] + (task - task_ofs[h]) * SEG_ITEMS;
     const uint32_t i1 = min(i0 + SEG_ITEMS, P.wofs[p + 1]);
     const uint32_t nk = i1 - i0;
+    int live = 0;  // does any item of this task walk anything?
     for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
       uint2 r = P.witem[i0 + k];
       const bool mine = !P.route || P.route[i0 + k] == V_PROBE;
@@ -529,6 +530,17 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       endp[k] = r.y;
       nextv[k] = r.x < r.y ? P.adj[r.x] : NONE;
       ih[k] = mine ? 0u : NONE;  // NONE: the item belongs to another route
+      live |= r.x < r.y;
+    }
+    if (!__syncthreads_or(live)) {  // nothing to walk: results only (zero hits)
+      if (MODE == M_LIST_COUNT || MODE == M_TIMED)
+        for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x)
+          if (ih[k] != NONE) {
+            if (MODE == M_LIST_COUNT) P.tcnt[P.wedge[i0 + k]] = 0;
+            else P.cyc[P.wedge[i0 + k]] = 0;
+          }
+      __syncthreads();
+      continue;
     }
     const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;

@@ -312,8 +312,10 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
   L.dev = c.take<DevScalars>(1);
   L.keysA = c.take<uint64_t>(Es);
   L.keysB = c.take<uint64_t>(Es);
-  L.flags = c.take<uint32_t>(Es + 1);
-  L.pos = c.take<uint32_t>(Es + 1);
+  // flags and pos are dead once the work items exist; the staging-free item
+  // list of the counting phase reuses them (8 (E+1) bytes)
+  L.flags = c.take<uint32_t>(2 * (Es + 1));
+  L.pos = L.flags + (Es + 1);
   L.deg = c.take<uint32_t>(ns);
   L.ek0 = c.take<uint32_t>(ns); L.ek1 = c.take<uint32_t>(ns);
   L.ev0 = c.take<uint32_t>(ns); L.ev1 = c.take<uint32_t>(ns);
@@ -338,7 +340,7 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
   }
   L.route = c.take<uint8_t>(Es);
   L.rprobe = c.take<uint32_t>(ns);
-  L.eplist = c.take<uint2>(Es);
+  L.eplist = reinterpret_cast<uint2*>(L.flags);
   int64_t big = Es > ns ? Es : ns;  // the eta sort and the pivot scans run over n
   size_t tb = radix_tmp_bytes(big);
   size_t sb = scan_tmp_bytes(big + 1);

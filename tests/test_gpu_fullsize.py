@@ -1,0 +1,179 @@
+"""Full-size configurations, checked on sampled outputs the oracle computes one
+by one and on properties that hold at any size.
+
+config 2  R-MAT scale 20: m and W against the oracle; t(v) of sampled
+          vertices (oracle, edges among N(v)); count = per-vertex total / 3 =
+          listed triangles; the full list in canonical order (every triangle
+          checked on the GPU against an eta computed here from the raw edges);
+          sampled triangles are triangles of the input.
+config 3  R-MAT scale 24: the same with the list streamed in chunks of 2^28
+          triangles and t(v) sampled straight from the raw edge list.
+config 4  R-MAT scale 27 and Chung-Lu 2^27 (gamma 2.1, mean degree 32):
+          count and per-vertex counts; sampled t(v) from the raw edge list;
+          the learned route and the global-bitmap hub path agree.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import u64
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def aot():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2006_11494_gb300 as m
+    return m
+
+
+def edge_keys(s, d):
+    """Sorted distinct undirected edges of a raw pair list as uint64 keys."""
+    a = np.minimum(s, d).astype(np.uint64)
+    b = np.maximum(s, d).astype(np.uint64)
+    keep = a != b
+    return np.unique((a[keep] << np.uint64(32)) | b[keep])
+
+
+def eta_ranks(n, keys):
+    """Degree non-increasing, ties by smaller id (plain definition)."""
+    deg = np.bincount((keys >> np.uint64(32)).astype(np.int64), minlength=n) + \
+        np.bincount((keys & np.uint64(0xffffffff)).astype(np.int64), minlength=n)
+    order = np.lexsort((np.arange(n), -deg))
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    return rank, deg
+
+
+def has_edges(keys, x, y):
+    a = np.minimum(x, y).astype(np.uint64)
+    b = np.maximum(x, y).astype(np.uint64)
+    q = (a << np.uint64(32)) | b
+    pos = np.searchsorted(keys, q)
+    pos = np.minimum(pos, len(keys) - 1)
+    return keys[pos] == q
+
+
+class ListChecker:
+    """Canonical order of streamed chunks, checked on the GPU: ranks strictly
+    increasing inside a triangle and lexicographically across triangles."""
+
+    def __init__(self, rank):
+        import torch
+        self.rank = torch.from_numpy(rank).cuda()
+        self.last = None
+        self.total = 0
+
+    def feed(self, tri):
+        import torch
+        r = self.rank[tri.long()]
+        assert bool((r[:, 0] < r[:, 1]).all()) and bool((r[:, 1] < r[:, 2]).all())
+        if self.last is not None:
+            r = torch.cat([self.last[None], r])
+        a, b = r[:-1], r[1:]
+        gt = (b[:, 0] > a[:, 0]) | ((b[:, 0] == a[:, 0]) & ((b[:, 1] > a[:, 1]) |
+                                                           ((b[:, 1] == a[:, 1]) & (b[:, 2] > a[:, 2]))))
+        assert bool(gt.all())
+        self.last = r[-1].clone()
+        self.total += tri.shape[0]
+
+
+def stream_list(aot, g, cap, rank, keys, samples_per_chunk, rng):
+    import torch
+    out = torch.empty(3 * cap, dtype=torch.int32, device="cuda")
+    chk = ListChecker(rank)
+    cursor = 0
+    while True:
+        k, nxt = aot.aot_list(g.handle, aot.ROUTE_PLAIN, cursor, out, cap)
+        if k == 0:
+            break
+        tri = out[: 3 * k].view(-1, 3)
+        chk.feed(tri)
+        idx = rng.integers(0, k, samples_per_chunk)
+        t = tri[torch.from_numpy(idx).cuda()].cpu().numpy()
+        assert has_edges(keys, t[:, 0], t[:, 1]).all()
+        assert has_edges(keys, t[:, 1], t[:, 2]).all()
+        assert has_edges(keys, t[:, 0], t[:, 2]).all()
+        cursor = nxt
+        if k < cap:
+            break
+    return chk.total
+
+
+def orient(aot, n, s, d, flags=0):
+    import torch
+    return aot.OrientedGraph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n, flags)
+
+
+def test_config2_rmat20(aot):
+    rng = np.random.default_rng(20)
+    n, s, d = gg.rmat_cfg(20, 2)
+    ref = oracle.Graph(n, s, d)
+    g = orient(aot, n, s, d)
+    assert g.m == ref.m
+    assert g.info["W"] == ref.costs()["walk"]
+    T = g.count()
+    T2, t = g.count_per_vertex()
+    t = u64(t)
+    assert T == T2 and int(t.sum()) == 3 * T
+    deg = ref.degrees()
+    cand = np.nonzero((deg > 0) & (deg <= 3000))[0]
+    for v in list(rng.choice(cand, 25, replace=False)) + [int(cand[np.argmax(deg[cand])])]:
+        assert t[v] == ref.vertex_count(int(v)), v
+    keys = edge_keys(s, d)
+    assert len(keys) == ref.m
+    rank, _ = eta_ranks(n, keys)
+    assert stream_list(aot, g, 1 << 26, rank, keys, 2000, rng) == T
+
+
+def test_config3_rmat24_streamed_listing(aot):
+    rng = np.random.default_rng(24)
+    n, s, d = gg.rmat_cfg(24, 3)
+    g = orient(aot, n, s, d)
+    keys = edge_keys(s, d)
+    assert g.m == len(keys)
+    T = g.count()
+    T2, t = g.count_per_vertex()
+    t = u64(t)
+    assert T == T2 and int(t.sum()) == 3 * T
+    rank, deg = eta_ranks(n, keys)
+    cand = np.nonzero((deg > 0) & (deg <= 20000))[0]
+    pick = np.concatenate([rng.choice(cand, 3, replace=False), [cand[np.argmax(deg[cand])]]]).astype(np.int32)
+    assert np.array_equal(oracle.stream_vertex_counts(n, s, d, pick), t[pick])
+    del t
+    g.close()
+    g = orient(aot, n, s, d)  # with the listing arrays
+    assert stream_list(aot, g, 1 << 28, rank, keys, 300, rng) == T
+
+
+@pytest.mark.parametrize("which", ["rmat27", "chunglu27"])
+def test_config4_billion_edges(aot, which):
+    import torch
+    from paper_2006_11494_gb300 import router
+    rng = np.random.default_rng(27)
+    if which == "rmat27":
+        n, s, d = gg.rmat_cfg(27, 4)
+    else:
+        n = 1 << 27
+        s, d = gg.chunglu(n, 2.1, 32.0, seed=5)
+    g = orient(aot, n, s, d, aot.FLAG_NO_LIST)
+    assert g.m > 1_000_000_000
+    T = g.count()
+    T2, t = g.count_per_vertex()
+    t = u64(t)
+    assert T == T2 and int(t.sum()) == 3 * T and T > 0
+    deg_sample = rng.choice(n, 200000, replace=False).astype(np.int32)
+    tv = t[deg_sample]
+    pick = np.concatenate([deg_sample[np.nonzero(tv)[0][:2]], deg_sample[:1]]).astype(np.int32)
+    assert np.array_equal(oracle.stream_vertex_counts(n, s, d, pick), t[pick])
+    model = router.load()
+    assert model is not None
+    aot.aot_graph_set_router(g.handle, model)
+    assert g.count(aot.ROUTE_LEARNED) == T
+    g.set_tuning(hub_mode=1)  # hubs on the multi-CTA global-bitmap path
+    assert g.count() == T
