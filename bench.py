@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=23,
                     help="log2 of the edge-stream prefix the CPU baseline runs on")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the learned-vs-plain and eta-order ablation measurements")
     return ap.parse_args()
 
 
@@ -143,8 +146,16 @@ def bytes_per_kernel(info, bins, E, n):
 
     out["k_warp_pivots/vertex"] = (walk_bytes("warp"), 1)
     out["k_cta_pivots/vertex"] = (walk_bytes("cta"), 1)
+    out["k_seg_pivots/vertex"] = (walk_bytes("hub"), 1)
     out["k_hub_walk/vertex"] = (walk_bytes("hub") - 4 * bins["hub"]["staged"], None)
     return out
+
+
+def count_phase_bytes(info, n):
+    """Algorithmic bytes of the whole count phase: stage N+(p) (4 S), the
+    items (12 m: walk range and walked vertex), the walked entries (4 W), the
+    pivot offsets (8 (n+1)) and the per-vertex output (8 n)."""
+    return 4 * info["S"] + 12 * info["m"] + 4 * info["W"] + 8 * (n + 1) + 8 * n
 
 
 # ------------------------------------------------------------------ ours
@@ -184,6 +195,14 @@ def run_ours(a):
             import torch.distributed as dist
             dist.barrier()
 
+    # autotune once on this workload (per-vertex mode); later graphs inherit it
+    tuning, tune_ms = None, None
+    if not a.no_tune:
+        h = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST, ws, stream)
+        t, tune_ms = aot.aot_tune(h, 1, 1, stream)
+        aot.aot_set_default_tuning(t)
+        tuning = t.as_dict()
+        aot.aot_graph_destroy(h)
     # warm-up (also the reference values of this run)
     for _ in range(max(a.warmup, 3)):
         h = step(src, dst)
@@ -215,17 +234,46 @@ def run_ours(a):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    # count phase alone (plain route), for context
+    # count phase alone, for context: plain route, learned route, count mode
+    def phase_ms(fn, reps):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record(stream)
+        for _ in range(reps):
+            fn()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        return c0.elapsed_time(c1) / reps
+
     h = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST, ws, stream)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    c0.record(stream)
-    for _ in range(a.steps):
-        aot.aot_count_per_vertex(h, route, counts, want_total=False, stream=stream)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    count_ms = c0.elapsed_time(c1) / a.steps
+    count_ms = phase_ms(lambda: aot.aot_count_per_vertex(h, route, counts, want_total=False,
+                                                         stream=stream), a.steps)
+    extras = {}
+    if not a.no_extras:
+        from paper_2006_11494_gb300 import router as rt
+        count_only_ms = phase_ms(lambda: aot.aot_count(h, aot.ROUTE_PLAIN, stream), a.steps)
+        extras["count_only_ms"] = count_only_ms
+        model = rt.load()
+        if model is not None:
+            aot.aot_graph_set_router(h, model)
+            plain = phase_ms(lambda: aot.aot_count(h, aot.ROUTE_PLAIN, stream), a.steps)
+            learned = phase_ms(lambda: aot.aot_count(h, aot.ROUTE_LEARNED, stream), a.steps)
+            forced = rt.with_margin(model, 0.0)  # the network's own choice, no plain-rule margin
+            aot.aot_graph_set_router(h, forced)
+            learned0 = phase_ms(lambda: aot.aot_count(h, aot.ROUTE_LEARNED, stream), a.steps)
+            aot.aot_graph_set_router(h, None)
+            extras["learned_vs_plain"] = {
+                "plain_count_ms": plain, "learned_count_ms": learned,
+                "speedup": plain / learned, "learned_margin0_count_ms": learned0,
+                "speedup_margin0": plain / learned0,
+                "note": "model trained on R-MAT s18-22 timings; the plain rule judged it on a held-out graph"}
     aot.aot_graph_destroy(h)
+    if not a.no_extras:
+        ha = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST | aot.ETA_DEG_ASC, ws, stream)
+        ia = aot.aot_graph_info(ha)
+        extras["ablation_eta_degree_ascending"] = {
+            "W": ia["W"], "count_only_ms": phase_ms(lambda: aot.aot_count(ha, aot.ROUTE_PLAIN, stream), a.steps)}
+        aot.aot_graph_destroy(ha)
 
     # end to end: pinned host edge list in, per-vertex counts out, every step
     e2e = None
@@ -298,7 +346,11 @@ def run_ours(a):
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "triangles_per_s": world * T / (ms / 1e3),
         "count_phase": {"ms": count_ms, "oriented_edges_per_s": info["m"] / (count_ms / 1e3),
-                        "triangles_per_s": T / (count_ms / 1e3), "probes_per_s": info["W"] / (count_ms / 1e3)},
+                        "triangles_per_s": T / (count_ms / 1e3), "probes_per_s": info["W"] / (count_ms / 1e3),
+                        "alg_bytes": count_phase_bytes(info, n),
+                        "hbm_frac": count_phase_bytes(info, n) / (count_ms / 1e3) / 1e9 / measured_peak()[0]},
+        "tuning": {"autotuned": tuning is not None, "values": tuning, "tune_best_ms": tune_ms},
+        "extras": extras,
         "bins": bins,
         "roofline": roof,
         "kernels": kernels,

@@ -406,12 +406,45 @@ __device__ __forceinline__ uint4 seg_load(const uint32_t* __restrict__ adj, uint
 // (lists are eta-sorted) and its value is returned in next_val.
 // x: cursor (updated), hk: hits of the item so far (updated; listing ranks).
 template <int MODE>
+__device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t e[4],
+                                               uint32_t& lane_hits, uint64_t& found, uint32_t& hk,
+                                               uint32_t p, uint32_t vj, uint64_t tb) {
+  const uint32_t c = (uint32_t)__popc(hits);
+  found += c;
+  if (MODE == M_VERTEX) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (hits & (1u << j)) atomicAdd((unsigned long long*)&P.tv[e[j]], 1ull);
+  }
+  if (MODE == M_LIST_WRITE) {
+    const uint32_t incl = warp_inclusive_scan(c);
+    uint64_t r = tb + hk + (incl - c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
+    hk += __shfl_sync(FULL, incl, 31);
+  } else {
+    lane_hits += c;
+  }
+}
+
+// One warp advances one item through the segment [segLo, segHi): rounds of
+// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
+// 128-bit load), with the next round's load issued before the current round
+// is tested (two rounds in flight per warp).  A round that lies wholly inside
+// the walk range and the segment (one warp vote: the lists are eta-sorted)
+// takes the fast path: every entry is a bitmap test, nothing else.  Other
+// rounds test each entry: b = w - segLo is a hit iff b < width and its bit is
+// set, and the first entry >= segHi ends the visit (its value is returned in
+// next_val).  x: cursor (updated), hk: hits of the item so far (updated).
+template <int MODE>
 __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t segLo,
                                               uint32_t segHi, uint32_t& x, uint32_t y, uint32_t& hk,
                                               uint32_t p, uint32_t vj, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
   const unsigned lane = lane_id();
   const uint32_t width = segHi - segLo;
+  uint32_t lane_hits = 0;
   next_val = NONE;
   if (x >= y) return;
   uint32_t base = x & ~3u;
@@ -420,6 +453,22 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
     const uint32_t idx0 = base + 4 * lane;
     const uint4 vn = seg_load(P.adj, idx0 + 128, y);  // prefetch the next round
     const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+    const bool full = base >= x && base + 128 <= y &&
+                      __all_sync(FULL, v.x >= segLo && v.w < segHi);
+    if (full) {
+      unsigned hits = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t b = e[j] - segLo;
+        hits |= ((bm[b >> 5] >> (b & 31)) & 1u) << j;
+      }
+      seg_count_hits<MODE>(P, hits, e, lane_hits, found, hk, p, vj, tb);
+      base += 128;
+      x = base;
+      if (x >= y) break;
+      v = vn;
+      continue;
+    }
     uint32_t stop = NONE, stop_val = NONE;
     unsigned hits = 0;
 #pragma unroll
@@ -433,38 +482,21 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
       const uint32_t b = e[j] - segLo;
       if (valid && b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) hits |= 1u << j;
     }
-    const uint32_t c = (uint32_t)__popc(hits);
-    found += c;
-    if (MODE == M_VERTEX) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (hits & (1u << j)) atomicAdd((unsigned long long*)&P.tv[e[j]], 1ull);
-    }
-    if (MODE == M_LIST_WRITE) {
-      const uint32_t incl = warp_inclusive_scan(c);
-      uint64_t r = tb + hk + (incl - c);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
-      hk += __shfl_sync(FULL, incl, 31);
-    } else if (MODE != M_COUNT) {
-      hk += warp_sum(c);
-    }
+    seg_count_hits<MODE>(P, hits, e, lane_hits, found, hk, p, vj, tb);
     const uint32_t first_stop = __reduce_min_sync(FULL, stop);
     if (first_stop != NONE) {
       const unsigned owner = __ballot_sync(FULL, stop == first_stop);
       next_val = __shfl_sync(FULL, stop_val, __ffs(owner) - 1);
       x = first_stop;
-      return;
+      break;
     }
     base += 128;
     x = base;
-    if (x >= y) {
-      x = y;
-      return;
-    }
+    if (x >= y) break;
     v = vn;
   }
+  if (x > y) x = y;
+  if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += warp_sum(lane_hits);
 }
 
 template <int MODE>
