@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-sample-log2", type=int, default=23,
                     help="log2 of the edge-stream prefix the CPU baseline runs on")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON object of aot_tuning fields to use instead of autotuning")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned-vs-plain and eta-order ablation measurements")
     return ap.parse_args()
@@ -60,6 +62,24 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (the step time every rank reports);
+    x itself when not running distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, max_ms: float, world: int) -> float:
+    """Whole-job throughput of N independent replicas: the units all ranks
+    processed divided by the slowest rank's time per step."""
+    return world * units_per_rank / (max_ms / 1e3)
 
 
 def measured_peak():
@@ -197,7 +217,13 @@ def run_ours(a):
 
     # autotune once on this workload (per-vertex mode); later graphs inherit it
     tuning, tune_ms = None, None
-    if not a.no_tune:
+    if a.tuning:
+        t = aot.aot_get_default_tuning()
+        for k, v in json.loads(a.tuning).items():
+            setattr(t, k, v)
+        aot.aot_set_default_tuning(t)
+        tuning = t.as_dict()
+    elif not a.no_tune:
         h = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST, ws, stream)
         t, tune_ms = aot.aot_tune(h, 1, 1, stream)
         aot.aot_set_default_tuning(t)
@@ -227,12 +253,7 @@ def run_ours(a):
         barrier()
     prof = aot.aot_profile_end()
     launches = aot.aot_kernel_launches() - l0
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
 
     # count phase alone, for context: plain route, learned route, count mode
     def phase_ms(fn, reps):
@@ -292,13 +313,8 @@ def run_ours(a):
             stream.synchronize()
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / a.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * info["m"] / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+        e2e = {"value": replica_value(info["m"], e_ms, world), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n}
         del d_src, d_dst
 
@@ -332,7 +348,7 @@ def run_ours(a):
     if not a.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(a.scale, a.seed, a.cpu_sample_log2, h_src.numpy(), h_dst.numpy())
 
-    value = world * info["m"] / (ms / 1e3)
+    value = replica_value(info["m"], ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -349,7 +365,7 @@ def run_ours(a):
                         "triangles_per_s": T / (count_ms / 1e3), "probes_per_s": info["W"] / (count_ms / 1e3),
                         "alg_bytes": count_phase_bytes(info, n),
                         "hbm_frac": count_phase_bytes(info, n) / (count_ms / 1e3) / 1e9 / measured_peak()[0]},
-        "tuning": {"autotuned": tuning is not None, "values": tuning, "tune_best_ms": tune_ms},
+        "tuning": {"autotuned": tuning is not None and not a.tuning, "values": tuning, "tune_best_ms": tune_ms},
         "extras": extras,
         "bins": bins,
         "roofline": roof,
