@@ -148,10 +148,11 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * per pivot (shared-memory hash table; cta_max_outdeg <= 8192), larger ->
  * hub path.  hub_mode 0: a shared-memory bitmap over eta ranks, swept one
  * segment of seg_bits ranks at a time (a multiple of 32 in [1024, 1572864])
- * by a CTA per (pivot, block of 2048 items); hub_mode 1: global bitmaps of
- * n bits, hub_bitmaps (1..32) hubs at a time, all CTAs sharing their items.
- * cta_threads is a multiple of 32 in [64, 1024].  Tuning never changes
- * results, only speed. */
+ * by a CTA per (pivot, block of 1536 items), items with at least seg_long
+ * entries walked by a warp, shorter ones by a thread each; hub_mode 1:
+ * global bitmaps of n bits, hub_bitmaps (1..32) hubs at a time, all CTAs
+ * sharing their items.  cta_threads is a multiple of 32 in [64, 1024].
+ * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
   uint32_t cta_max_outdeg;
@@ -159,6 +160,7 @@ typedef struct {
   int32_t hub_bitmaps;
   int32_t hub_mode;
   uint32_t seg_bits;
+  uint32_t seg_long;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

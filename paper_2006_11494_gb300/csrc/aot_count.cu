@@ -353,12 +353,13 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
 // the bits.  Items keep cursor, end and hit count in shared memory, so one
 // item's hits come out in ascending w order (the listing order).
 constexpr int SEG_THREADS = 1024;
-constexpr uint32_t SEG_ITEMS = 2048;
+constexpr uint32_t SEG_ITEMS = 1536;
+
 constexpr uint32_t SEG_BITS_MAX = 1536u * 1024u;  // 192 KB of bitmap at most
 constexpr uint32_t NONE = 0xffffffffu;
-// bitmap + per item: cursor, end, next walked value, hits
+// bitmap + per item: cursor, end, next walked value, hits; list of long items; long flags
 constexpr size_t seg_smem_bytes(uint32_t seg_bits) {
-  return (size_t)(seg_bits / 32) * 4 + 4 * (size_t)SEG_ITEMS * 4;
+  return (size_t)(seg_bits / 32) * 4 + 5 * (size_t)SEG_ITEMS * 4 + SEG_ITEMS;
 }
 
 __global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
@@ -499,9 +500,49 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
   if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += warp_sum(lane_hits);
 }
 
+// One thread advances one short item through the segment [segLo, segHi):
+// four entries loaded at a time, stopping at the first entry >= segHi, whose
+// value is returned in nv.  Hits come out in order (listing ranks hk + i).
+template <int MODE>
+__device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t* bm, uint32_t segLo,
+                                               uint32_t segHi, uint32_t& x, uint32_t y,
+                                               uint32_t& nv, uint32_t& hk, uint32_t p, uint32_t vj,
+                                               uint64_t tb, uint64_t& found) {
+  const uint32_t width = segHi - segLo;
+  nv = NONE;
+  while (x < y) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = x + j < y ? __ldg(P.adj + x + j) : NONE;
+    uint32_t used = 0;
+    bool stop = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (stop) continue;
+      if (w[j] >= segHi) {  // also the padding past y (NONE)
+        stop = true;
+        nv = w[j];
+        continue;
+      }
+      ++used;
+      const uint32_t b = w[j] - segLo;
+      if (b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) {
+        ++found;
+        if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[j]], 1ull);
+        if (MODE == M_LIST_WRITE) emit(P, tb + hk, p, vj, w[j]);
+        ++hk;
+      }
+    }
+    x += used;
+    if (stop) break;
+  }
+  if (x >= y) nv = NONE;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
-                                                               uint32_t nh, uint32_t seg_bits) {
+                                                               uint32_t nh, uint32_t seg_bits,
+                                                               uint32_t seg_long) {
   extern __shared__ uint32_t seg_sm[];
   const uint32_t seg_words = seg_bits / 32;
   uint32_t* bm = seg_sm;
@@ -509,7 +550,9 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
   uint32_t* endp = cur + SEG_ITEMS;
   uint32_t* nextv = endp + SEG_ITEMS;
   uint32_t* ih = nextv + SEG_ITEMS;
-  __shared__ uint32_t s_task, s_hub, s_pe, s_next;
+  uint32_t* longs = ih + SEG_ITEMS;                              // long items of the task
+  uint8_t* islong = reinterpret_cast<uint8_t*>(longs + SEG_ITEMS);
+  __shared__ uint32_t s_task, s_hub, s_pe, s_next, s_nlong;
   __shared__ unsigned long long s_hits, s_stage;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
   const uint32_t ntasks = task_ofs[nh];
@@ -520,6 +563,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       s_task = atomicAdd(&P.dev->counters[Q_SEG], 1u);
       s_hits = 0;
       s_stage = 0;
+      s_nlong = 0;
     }
     __syncthreads();
     const uint32_t task = s_task;
@@ -563,6 +607,9 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       nextv[k] = r.x < r.y ? P.adj[r.x] : NONE;
       ih[k] = mine ? 0u : NONE;  // NONE: the item belongs to another route
       live |= r.x < r.y;
+      const bool lg = r.y - r.x >= seg_long;  // long items are walked warp-wide
+      islong[k] = lg;
+      if (lg) longs[atomicAdd(&s_nlong, 1u)] = k;
     }
     if (!__syncthreads_or(live)) {  // nothing to walk: results only (zero hits)
       if (MODE == M_LIST_COUNT || MODE == M_TIMED)
@@ -595,11 +642,31 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         }
         __syncthreads();
         if (MODE == M_TIMED && threadIdx.x == 0) s_stage += (unsigned long long)(clock64() - tset0) * (blockDim.x >> 5);
+        // short items: a thread each
+        for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+          if (islong[k] || nextv[k] >= segHi) continue;
+          uint32_t x = cur[k], hk = ih[k], nv;
+          uint32_t vj = 0;
+          uint64_t tb = 0;
+          if (MODE == M_LIST_WRITE) {
+            vj = P.wvert[i0 + k];
+            tb = P.toff[P.wedge[i0 + k]];
+          }
+          const long long tv0 = MODE == M_TIMED ? clock64() : 0;
+          seg_walk_short<MODE>(P, bm, segLo, segHi, x, endp[k], nv, hk, p, vj, tb, found);
+          if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
+          cur[k] = x;
+          nextv[k] = nv;
+          ih[k] = hk;
+        }
+        // long items: a warp each
+        const uint32_t nlong = s_nlong;
         while (true) {
-          uint32_t k = 0;
-          if (lane == 0) k = atomicAdd(&s_next, 1u);
-          k = __shfl_sync(FULL, k, 0);
-          if (k >= nk) break;
+          uint32_t g = 0;
+          if (lane == 0) g = atomicAdd(&s_next, 1u);
+          g = __shfl_sync(FULL, g, 0);
+          if (g >= nlong) break;
+          const uint32_t k = longs[g];
           if (nextv[k] >= segHi) continue;  // nothing of this item in the segment
           uint32_t x = cur[k], hk = ih[k], nv;
           const uint32_t y = endp[k];
@@ -753,7 +820,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
-          P, task_ofs, nh, seg_bits);
+          P, task_ofs, nh, seg_bits, g->tune.seg_long);
     AOT_TRY(last_launch());
   } else if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
@@ -1028,6 +1095,12 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
     for (uint32_t w : warps) {
       aot_tuning t = cur;
       t.warp_max_outdeg = w <= t.cta_max_outdeg ? w : t.cta_max_outdeg;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t longs[] = {64u, 128u, 256u, 512u};
+    for (uint32_t sl : longs) {
+      aot_tuning t = cur;
+      t.seg_long = sl;
       AOT_TRY(trial(t));
     }
     const uint32_t segs[] = {1572864u, 1048576u};
