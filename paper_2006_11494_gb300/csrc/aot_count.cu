@@ -357,17 +357,11 @@ constexpr uint32_t SEG_ITEMS = 1536;
 
 constexpr uint32_t SEG_BITS_MAX = 1536u * 1024u;  // 192 KB of bitmap at most
 constexpr uint32_t NONE = 0xffffffffu;
-// bitmap + per item: cursor, end, next walked value, hits; list of long items; long flags
+// bitmap + a zero guard word (answers every probe past the bitmap) and three
+// pad words + per item: cursor, end, next walked value, hits; list of long
+// items; long flags
 constexpr size_t seg_smem_bytes(uint32_t seg_bits) {
-  return (size_t)(seg_bits / 32) * 4 + 5 * (size_t)SEG_ITEMS * 4 + SEG_ITEMS;
-}
-
-__global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
-                                  const uint32_t* __restrict__ wofs, uint32_t* __restrict__ cnt) {
-  uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= nh) return;
-  uint32_t p = pivots[h];
-  cnt[h] = (wofs[p + 1] - wofs[p] + SEG_ITEMS - 1) / SEG_ITEMS;
+  return (size_t)(seg_bits / 32 + 4) * 4 + 5 * (size_t)SEG_ITEMS * 4 + SEG_ITEMS;
 }
 
 // first index in [lo, hi) with a[idx] >= key (a sorted); all 32 lanes call it
@@ -390,28 +384,57 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
   return lo + (uint32_t)__popc(__ballot_sync(FULL, less));
 }
 
-// One warp advances one item through the segment [segLo, segHi): rounds of
-// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
-// 128-bit load).  An entry b = w - segLo is a hit iff b < width and its bit
-// is set; the first entry >= segHi ends the visit (lists are eta-sorted).
-// x: cursor (updated), hk: hits of the item so far (updated; listing ranks).
-__device__ __forceinline__ uint4 seg_load(const uint32_t* __restrict__ adj, uint32_t idx0, uint32_t y) {
-  return idx0 < y ? __ldg(reinterpret_cast<const uint4*>(adj + idx0)) : make_uint4(NONE, NONE, NONE, NONE);
+constexpr uint32_t SEG_MAXB = 512;  // segment bounds of one pivot held in shared memory
+
+// Per hub pivot: its tasks, and its segments + 1 (the bounds of N+(p) that
+// split its rank range [min N+(p), max N+(p)] into segments of seg_bits).
+__global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
+                                  const uint32_t* __restrict__ wofs, const uint32_t* __restrict__ off,
+                                  const uint32_t* __restrict__ adj, uint32_t seg_bits,
+                                  uint32_t* __restrict__ cnt, uint32_t* __restrict__ nbound) {
+  uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= nh) return;
+  uint32_t p = pivots[h];
+  cnt[h] = (wofs[p + 1] - wofs[p] + SEG_ITEMS - 1) / SEG_ITEMS;
+  const uint32_t lo = adj[off[p]], hi = adj[off[p + 1] - 1] + 1;  // hubs have deg+ > 0
+  nbound[h] = (hi - lo + seg_bits - 1) / seg_bits + 1;
 }
 
-// One warp advances one item through the segment [segLo, segHi): rounds of
-// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
-// 128-bit load), with the next round's load issued before the current round
-// is tested (two rounds in flight per warp).  An entry b = w - segLo is a hit
-// iff b < width and its bit is set; the first entry >= segHi ends the visit
-// (lists are eta-sorted) and its value is returned in next_val.
-// x: cursor (updated), hk: hits of the item so far (updated; listing ranks).
+// Segment bounds of every hub pivot, a warp per pivot: bound s is the first
+// position of N+(p) holding a rank >= min N+(p) + s * seg_bits (bound 0 is the
+// list start, the last one its end).  Written only when they all fit in cap.
+__global__ void k_seg_bounds(const uint32_t* __restrict__ pivots, uint32_t nh,
+                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                             uint32_t seg_bits, const uint32_t* __restrict__ bofs, uint32_t* __restrict__ bnd,
+                             uint64_t cap) {
+  if ((uint64_t)bofs[nh] > cap) return;
+  const unsigned lane = lane_id();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
+    const uint32_t p = pivots[h];
+    const uint32_t pbeg = off[p], pend = off[p + 1];
+    const uint32_t lo = adj[pbeg];
+    const uint32_t nb = bofs[h + 1] - bofs[h];  // segments + 1
+    uint32_t* out = bnd + bofs[h];
+    uint32_t pc = pbeg;
+    if (lane == 0) out[0] = pbeg;
+    for (uint32_t sgm = 1; sgm + 1 < nb; ++sgm) {
+      pc = warp_lower_bound(adj, pc, pend, lo + sgm * seg_bits);
+      if (lane == 0) out[sgm] = pc;
+    }
+    if (lane == 0) out[nb - 1] = pend;
+  }
+}
+
+
+// Hits of one round: per-lane count, and in per-vertex and listing modes the
+// third vertices (listing ranks follow the warp's lane order).
 template <int MODE>
 __device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t e[4],
-                                               uint32_t& lane_hits, uint64_t& found, uint32_t& hk,
-                                               uint32_t p, uint32_t vj, uint64_t tb) {
+                                               uint32_t& lane_hits, uint32_t& hk, uint32_t p,
+                                               uint32_t vj, uint64_t tb) {
   const uint32_t c = (uint32_t)__popc(hits);
-  found += c;
+  lane_hits += c;
   if (MODE == M_VERTEX) {
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -424,80 +447,105 @@ __device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, 
     for (int j = 0; j < 4; ++j)
       if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
     hk += __shfl_sync(FULL, incl, 31);
-  } else {
-    lane_hits += c;
   }
 }
 
-// One warp advances one item through the segment [segLo, segHi): rounds of
-// 128 entries, lane L holding the four entries at (x & ~3) + 4L .. +3 (one
-// 128-bit load), with the next round's load issued before the current round
-// is tested (two rounds in flight per warp).  A round that lies wholly inside
-// the walk range and the segment (one warp vote: the lists are eta-sorted)
-// takes the fast path: every entry is a bitmap test, nothing else.  Other
-// rounds test each entry: b = w - segLo is a hit iff b < width and its bit is
-// set, and the first entry >= segHi ends the visit (its value is returned in
-// next_val).  x: cursor (updated), hk: hits of the item so far (updated).
+// Takes the warp's next long item that has entries in the segment (nextv below
+// segHi) from the task's shared list and issues the load of its first round
+// (lane L: the four entries at (x & ~3) + 4L); k = NONE when the list is done.
+__device__ __forceinline__ void seg_next_visit(const uint32_t* __restrict__ adj, const uint32_t* longs,
+                                               uint32_t nlong, uint32_t* next, const uint32_t* nextv,
+                                               const uint32_t* cur, const uint32_t* endp, uint32_t segHi,
+                                               uint32_t& k, uint32_t& x, uint32_t& y, uint4& v) {
+  const unsigned lane = lane_id();
+  while (true) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(next, 1u);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= nlong) {
+      k = NONE;
+      x = y = 0;
+      v = make_uint4(0, 0, 0, 0);
+      return;
+    }
+    k = longs[g];
+    if (nextv[k] < segHi) break;  // else nothing of this item in the segment
+  }
+  x = cur[k];
+  y = endp[k];
+  v = __ldg(reinterpret_cast<const uint4*>(adj + (x & ~3u)) + lane);
+}
+
+// One warp advances one item through the segment [segLo, segHi) in rounds of
+// 128 entries: lane L holds the four entries at base + 4L .. +3 (one 128-bit
+// load, base = x rounded down to a multiple of 4), and the next round is loaded
+// while this one is probed.  An entry w is a hit iff it lies in [x, stop) and
+// bit b = w - segLo of the bitmap is set: entries below segLo wrap to a huge b,
+// and every b past the bitmap reads the zero guard word, so a probe needs no
+// range test.  The visit ends at stop, the first index >= x holding an entry
+// >= segHi, or y.  Lists are eta-sorted, so a vote on each lane's last entry
+// tells whether stop lies in this round; only that final round computes stop,
+// masks the entries from stop on (and, at y, the next list's entries), and
+// returns the entry at stop in next_val (NONE at y).  Only lane 0 of the first
+// round can hold entries below x.  The adjacency array is padded so that a
+// round starting below y never reads past the allocation.
+// x: cursor (updated), nxt: the first round (already loaded), hk: hits of the
+// item so far (updated).
 template <int MODE>
-__device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t segLo,
-                                              uint32_t segHi, uint32_t& x, uint32_t y, uint32_t& hk,
-                                              uint32_t p, uint32_t vj, uint64_t tb,
+__device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t seg_words,
+                                              uint32_t segLo, uint32_t segHi, uint32_t& x, uint32_t y,
+                                              uint4 nxt, uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
   const unsigned lane = lane_id();
-  const uint32_t width = segHi - segLo;
   uint32_t lane_hits = 0;
   next_val = NONE;
   if (x >= y) return;
   uint32_t base = x & ~3u;
-  uint4 v = seg_load(P.adj, base + 4 * lane, y);
+  const uint4* src = reinterpret_cast<const uint4*>(P.adj + base) + lane;
+  const unsigned first = lane == 0 ? (0xFu << (x & 3u)) & 0xFu : 0xFu;  // entries >= x
+  unsigned head = first;
   while (true) {
-    const uint32_t idx0 = base + 4 * lane;
-    const uint4 vn = seg_load(P.adj, idx0 + 128, y);  // prefetch the next round
+    const uint4 v = nxt;
+    const bool tail = base + 128 >= y;  // warp-uniform: this round reaches y
+    if (!tail) nxt = __ldg(src + 32);
     const uint32_t e[4] = {v.x, v.y, v.z, v.w};
-    const bool full = base >= x && base + 128 <= y &&
-                      __all_sync(FULL, v.x >= segLo && v.w < segHi);
-    if (full) {
-      unsigned hits = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t b = e[j] - segLo;
-        hits |= ((bm[b >> 5] >> (b & 31)) & 1u) << j;
-      }
-      seg_count_hits<MODE>(P, hits, e, lane_hits, found, hk, p, vj, tb);
-      base += 128;
-      x = base;
-      if (x >= y) break;
-      v = vn;
-      continue;
-    }
-    uint32_t stop = NONE, stop_val = NONE;
     unsigned hits = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const uint32_t idx = idx0 + j;
-      const bool valid = idx >= x && idx < y;
-      if (valid && e[j] >= segHi && stop == NONE) {
-        stop = idx;
-        stop_val = e[j];
-      }
       const uint32_t b = e[j] - segLo;
-      if (valid && b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) hits |= 1u << j;
+      const uint32_t word = bm[min(b >> 5, seg_words)];
+      hits |= (__funnelshift_r(word, word, b) & 1u) << j;
     }
-    seg_count_hits<MODE>(P, hits, e, lane_hits, found, hk, p, vj, tb);
-    const uint32_t first_stop = __reduce_min_sync(FULL, stop);
-    if (first_stop != NONE) {
-      const unsigned owner = __ballot_sync(FULL, stop == first_stop);
-      next_val = __shfl_sync(FULL, stop_val, __ffs(owner) - 1);
-      x = first_stop;
+    hits &= head;
+    const bool fin = __any_sync(FULL, v.w >= segHi) || tail;  // warp-uniform
+    uint32_t stop = NONE;
+    if (fin) {
+      const uint32_t idx0 = base + 4 * lane;
+      // entries below segHi, and those below x, are passed over
+      unsigned below = (unsigned)(e[0] < segHi) | ((unsigned)(e[1] < segHi) << 1) |
+                       ((unsigned)(e[2] < segHi) << 2) | ((unsigned)(e[3] < segHi) << 3);
+      below |= ~head & 0xFu;
+      const uint32_t j = (uint32_t)__ffs(~below) - 1u;  // 0..4
+      stop = min(__reduce_min_sync(FULL, j < 4 ? idx0 + j : NONE), y);
+      const uint32_t keep = idx0 < stop ? min(stop - idx0, 4u) : 0u;
+      hits &= (1u << keep) - 1u;
+      const uint32_t rel = stop - base;  // 0..128
+      const uint32_t r3 = rel & 3u;
+      const uint32_t at = r3 == 0 ? e[0] : r3 == 1 ? e[1] : r3 == 2 ? e[2] : e[3];
+      const uint32_t val = __shfl_sync(FULL, at, (rel >> 2) & 31u);
+      next_val = stop < y ? val : NONE;
+    }
+    seg_count_hits<MODE>(P, hits, e, lane_hits, hk, p, vj, tb);
+    if (fin) {
+      x = stop;
       break;
     }
+    head = 0xFu;
     base += 128;
-    x = base;
-    if (x >= y) break;
-    v = vn;
+    src += 32;
   }
-  if (x > y) x = y;
-  if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += warp_sum(lane_hits);
+  found += lane_hits;
+  if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += __reduce_add_sync(FULL, lane_hits);
 }
 
 // One thread advances one short item through the segment [segLo, segHi):
@@ -542,21 +590,26 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
 template <int MODE>
 __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
                                                                uint32_t nh, uint32_t seg_bits,
-                                                               uint32_t seg_long) {
+                                                               uint32_t seg_long,
+                                                               const uint32_t* __restrict__ bofs,
+                                                               const uint32_t* __restrict__ bnd,
+                                                               uint64_t bcap) {
   extern __shared__ uint32_t seg_sm[];
   const uint32_t seg_words = seg_bits / 32;
   uint32_t* bm = seg_sm;
-  uint32_t* cur = bm + seg_words;
+  uint32_t* cur = bm + seg_words + 4;
   uint32_t* endp = cur + SEG_ITEMS;
   uint32_t* nextv = endp + SEG_ITEMS;
   uint32_t* ih = nextv + SEG_ITEMS;
   uint32_t* longs = ih + SEG_ITEMS;                              // long items of the task
   uint8_t* islong = reinterpret_cast<uint8_t*>(longs + SEG_ITEMS);
   __shared__ uint32_t s_task, s_hub, s_pe, s_next, s_nlong;
+  __shared__ uint32_t s_bound[SEG_MAXB];  // this pivot's segment bounds (when they fit)
   __shared__ unsigned long long s_hits, s_stage;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
   const uint32_t ntasks = task_ofs[nh];
-  for (uint32_t i = threadIdx.x; i < seg_words; i += blockDim.x) bm[i] = 0;
+  const bool have_bounds = bnd != nullptr && (uint64_t)bofs[nh] <= bcap;
+  for (uint32_t i = threadIdx.x; i <= seg_words; i += blockDim.x) bm[i] = 0;  // + guard word
   uint64_t found = 0;
   while (true) {
     if (threadIdx.x == 0) {
@@ -589,6 +642,12 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       __syncthreads();
       continue;
     }
+    // the pivot's list and its segment bounds (read while the items load)
+    const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
+    const uint32_t nb = have_bounds ? bofs[h + 1] - bofs[h] : 0u;
+    const bool use_bounds = nb != 0 && nb <= SEG_MAXB;
+    if (use_bounds)
+      for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_bound[t] = bnd[bofs[h] + t];
     const uint32_t i0 = P.wofs[p] + (task - task_ofs[h]) * SEG_ITEMS;
     const uint32_t i1 = min(i0 + SEG_ITEMS, P.wofs[p + 1]);
     const uint32_t nk = i1 - i0;
@@ -621,19 +680,19 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       __syncthreads();
       continue;
     }
-    const uint32_t pbeg = P.off[p], pend = P.off[p + 1];
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
     uint32_t pc = pbeg;
     __syncthreads();
-    for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += seg_bits) {
+    uint32_t sgm = 0;
+    for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += seg_bits, ++sgm) {
       const uint32_t segHi = min(segLo + seg_bits, hi_rank);
-      if (wid == 0) {
+      if (!use_bounds && wid == 0) {
         const uint32_t pe = warp_lower_bound(P.adj, pc, pend, segHi);
         if (lane == 0) s_pe = pe;
       }
       if (threadIdx.x == 0) s_next = 0;
       __syncthreads();
-      const uint32_t pe = s_pe;
+      const uint32_t pe = use_bounds ? s_bound[sgm + 1] : s_pe;
       if (pe > pc) {
         const long long tset0 = MODE == M_TIMED ? clock64() : 0;
         for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
@@ -662,14 +721,11 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         // long items: a warp each
         const uint32_t nlong = s_nlong;
         while (true) {
-          uint32_t g = 0;
-          if (lane == 0) g = atomicAdd(&s_next, 1u);
-          g = __shfl_sync(FULL, g, 0);
-          if (g >= nlong) break;
-          const uint32_t k = longs[g];
-          if (nextv[k] >= segHi) continue;  // nothing of this item in the segment
-          uint32_t x = cur[k], hk = ih[k], nv;
-          const uint32_t y = endp[k];
+          uint32_t k, x, y;
+          uint4 v0;
+          seg_next_visit(P.adj, longs, nlong, &s_next, nextv, cur, endp, segHi, k, x, y, v0);
+          if (k == NONE) break;
+          uint32_t hk = ih[k], nv;
           uint32_t vj = 0;
           uint64_t tb = 0;
           if (MODE == M_LIST_WRITE) {
@@ -677,7 +733,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
             tb = P.toff[P.wedge[i0 + k]];
           }
           const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-          seg_walk_item<MODE>(P, bm, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+          seg_walk_item<MODE>(P, bm, seg_words, segLo, segHi, x, y, v0, hk, p, vj, tb, found, nv);
           if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
           __syncwarp();
           if (lane == 0) {
@@ -800,13 +856,34 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
   if (nh && g->tune.hub_mode == 0) {
     // segmented shared-memory bitmap: tasks = (pivot, block of SEG_ITEMS items)
     const uint32_t* dp = g->bin_pivots + nw + nc;
+    // hubinfo (4n words): task counts | task offsets | bound counts | bound
+    // offsets | bounds (what is left: the bounds are skipped when they do not fit)
+    const uint32_t seg_bits = g->tune.seg_bits;
+    const size_t n4 = 4 * (size_t)g->n;
     uint32_t* cnt = g->hubinfo;
     uint32_t* task_ofs = g->hubinfo + g->n;
+    uint32_t* nbound = g->hubinfo + 2 * (size_t)g->n;
+    uint32_t* bofs = nbound + nh;
+    uint32_t* bnd = bofs + nh + 1;
+    const size_t used = (size_t)(bnd - g->hubinfo);
+    // every pivot has at most ceil(n / seg_bits) segments: take the bounds only
+    // when that many fit (this also keeps the 32-bit offsets exact)
+    const uint64_t worst = (uint64_t)nh * (((uint64_t)g->n + seg_bits - 1) / seg_bits + 1);
+    const uint64_t room = used < n4 ? (uint64_t)(n4 - used) : 0;
+    const uint64_t bcap = worst <= room && worst < 0xffffffffull ? room : 0;
     AOT_KERNEL("k_seg_task_counts", s)
-      k_seg_task_counts<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, cnt);
+      k_seg_task_counts<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->adj, seg_bits, cnt,
+                                                         nbound);
     AOT_TRY(last_launch());
     AOT_TRY(scan_u32_u32(cnt, task_ofs, nh, g->scan_tmp, s));
-    const uint32_t seg_bits = g->tune.seg_bits;
+    if (bcap) {
+      AOT_TRY(scan_u32_u32(nbound, bofs, nh, g->scan_tmp, s));
+      int64_t bgrid = ((int64_t)nh * 32 + 255) / 256;
+      if (bgrid > (int64_t)sms * 8) bgrid = (int64_t)sms * 8;
+      AOT_KERNEL("k_seg_bounds", s)
+        k_seg_bounds<<<(unsigned)bgrid, 256, 0, s>>>(dp, nh, g->off, g->adj, seg_bits, bofs, bnd, bcap);
+      AOT_TRY(last_launch());
+    }
     const size_t seg_smem = seg_smem_bytes(seg_bits);
     static bool seg_attr[5] = {false, false, false, false, false};
     if (!seg_attr[MODE]) {
@@ -820,7 +897,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
-          P, task_ofs, nh, seg_bits, g->tune.seg_long);
+          P, task_ofs, nh, seg_bits, g->tune.seg_long, bofs, bcap ? bnd : nullptr, bcap);
     AOT_TRY(last_launch());
   } else if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
