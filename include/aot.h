@@ -149,7 +149,8 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * hub path.  hub_mode 0: a shared-memory bitmap over eta ranks, swept one
  * segment of seg_bits ranks at a time (a multiple of 32 in [1024, 1572864])
  * by a CTA per (pivot, block of 1536 items), items with at least seg_long
- * entries walked by a warp, shorter ones by a thread each; hub_mode 1:
+ * entries walked by a warp (in rounds of 256 entries while at least seg_wide
+ * entries remain, else of 128), shorter ones by a thread each; hub_mode 1:
  * global bitmaps of n bits, hub_bitmaps (1..32) hubs at a time, all CTAs
  * sharing their items.  cta_threads is a multiple of 32 in [64, 1024].
  * Tuning never changes results, only speed. */
@@ -161,6 +162,7 @@ typedef struct {
   int32_t hub_mode;
   uint32_t seg_bits;
   uint32_t seg_long;
+  uint32_t seg_wide;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

@@ -23,7 +23,7 @@ static bool tuning_valid(const aot_tuning* t) {
            t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
            (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
            t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
-           (t->seg_bits & 31) || t->seg_long > (1u << 30));
+           (t->seg_bits & 31) || t->seg_long > (1u << 30) || t->seg_wide > (1u << 30));
 }
 }  // namespace aot
 
@@ -37,6 +37,7 @@ extern "C" aot_status aot_set_default_tuning(const aot_tuning* t) {
   g_default_tuning.hub_mode = t->hub_mode;
   g_default_tuning.seg_bits = t->seg_bits;
   g_default_tuning.seg_long = t->seg_long;
+  g_default_tuning.seg_wide = t->seg_wide;
   return AOT_OK;
 }
 
@@ -57,6 +58,7 @@ extern "C" aot_status aot_get_default_tuning(aot_tuning* t) {
   t->hub_mode = d.hub_mode;
   t->seg_bits = d.seg_bits;
   t->seg_long = d.seg_long;
+  t->seg_wide = d.seg_wide;
   return AOT_OK;
 }
 
@@ -127,6 +129,7 @@ extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
   t->hub_mode = g->tune.hub_mode;
   t->seg_bits = g->tune.seg_bits;
   t->seg_long = g->tune.seg_long;
+  t->seg_wide = g->tune.seg_wide;
   return AOT_OK;
 }
 
@@ -140,6 +143,7 @@ extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, ao
   g->tune.hub_mode = t->hub_mode;
   g->tune.seg_bits = t->seg_bits;
   g->tune.seg_long = t->seg_long;
+  g->tune.seg_wide = t->seg_wide;
   aot_status st = bin_pivots(g, reinterpret_cast<cudaStream_t>(stream));
   if (st != AOT_OK) g->tune = old;
   return st;

@@ -429,34 +429,33 @@ __global__ void k_seg_bounds(const uint32_t* __restrict__ pivots, uint32_t nh,
 
 // Hits of one round: per-lane count, and in per-vertex and listing modes the
 // third vertices (listing ranks follow the warp's lane order).
-template <int MODE>
-__device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t e[4],
+template <int MODE, int E>
+__device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t (&e)[E],
                                                uint32_t& lane_hits, uint32_t& hk, uint32_t p,
                                                uint32_t vj, uint64_t tb) {
   const uint32_t c = (uint32_t)__popc(hits);
   lane_hits += c;
   if (MODE == M_VERTEX) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < E; ++j)
       if (hits & (1u << j)) atomicAdd((unsigned long long*)&P.tv[e[j]], 1ull);
   }
   if (MODE == M_LIST_WRITE) {
     const uint32_t incl = warp_inclusive_scan(c);
     uint64_t r = tb + hk + (incl - c);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < E; ++j)
       if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
     hk += __shfl_sync(FULL, incl, 31);
   }
 }
 
 // Takes the warp's next long item that has entries in the segment (nextv below
-// segHi) from the task's shared list and issues the load of its first round
-// (lane L: the four entries at (x & ~3) + 4L); k = NONE when the list is done.
-__device__ __forceinline__ void seg_next_visit(const uint32_t* __restrict__ adj, const uint32_t* longs,
-                                               uint32_t nlong, uint32_t* next, const uint32_t* nextv,
-                                               const uint32_t* cur, const uint32_t* endp, uint32_t segHi,
-                                               uint32_t& k, uint32_t& x, uint32_t& y, uint4& v) {
+// segHi) from the task's shared list; k = NONE when the list is done.
+__device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t nlong, uint32_t* next,
+                                               const uint32_t* nextv, const uint32_t* cur,
+                                               const uint32_t* endp, uint32_t segHi, uint32_t& k,
+                                               uint32_t& x, uint32_t& y) {
   const unsigned lane = lane_id();
   while (true) {
     uint32_t g = 0;
@@ -465,7 +464,6 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* __restrict__ adj,
     if (g >= nlong) {
       k = NONE;
       x = y = 0;
-      v = make_uint4(0, 0, 0, 0);
       return;
     }
     k = longs[g];
@@ -473,76 +471,92 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* __restrict__ adj,
   }
   x = cur[k];
   y = endp[k];
-  v = __ldg(reinterpret_cast<const uint4*>(adj + (x & ~3u)) + lane);
 }
 
 // One warp advances one item through the segment [segLo, segHi) in rounds of
-// 128 entries: lane L holds the four entries at base + 4L .. +3 (one 128-bit
-// load, base = x rounded down to a multiple of 4), and the next round is loaded
-// while this one is probed.  An entry w is a hit iff it lies in [x, stop) and
-// bit b = w - segLo of the bitmap is set: entries below segLo wrap to a huge b,
-// and every b past the bitmap reads the zero guard word, so a probe needs no
-// range test.  The visit ends at stop, the first index >= x holding an entry
-// >= segHi, or y.  Lists are eta-sorted, so a vote on each lane's last entry
-// tells whether stop lies in this round; only that final round computes stop,
-// masks the entries from stop on (and, at y, the next list's entries), and
-// returns the entry at stop in next_val (NONE at y).  Only lane 0 of the first
-// round can hold entries below x.  The adjacency array is padded so that a
-// round starting below y never reads past the allocation.
-// x: cursor (updated), nxt: the first round (already loaded), hk: hits of the
-// item so far (updated).
-template <int MODE>
+// 32 E entries: lane L holds the E entries at base + E L .. + E - 1 (E / 4
+// 128-bit loads, base = x rounded down to a multiple of E).  An entry w is a
+// hit iff it lies in [x, stop) and bit b = w - segLo of the bitmap is set:
+// entries below segLo wrap to a huge b, and every b past the bitmap reads the
+// zero guard word, so a probe needs no range test.  The visit ends at stop,
+// the first index >= x holding an entry >= segHi, or y.  Lists are eta-sorted,
+// so a vote on each lane's last entry tells whether stop lies in this round;
+// the vote comes before the next round's load (no round past the visit's end
+// is loaded), and only the final round computes stop, masks the entries from
+// stop on (and, at y, the next list's entries) and returns the entry at stop
+// in next_val (NONE at y).  Only lane 0 of the first round can hold entries
+// below x.  The adjacency array is padded so that a round starting below y
+// never reads past the allocation.
+// x: cursor (updated), hk: hits of the item so far (updated).
+template <int MODE, int E>
 __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t seg_words,
                                               uint32_t segLo, uint32_t segHi, uint32_t& x, uint32_t y,
-                                              uint4 nxt, uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
+                                              uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
+  static_assert(E == 4 || E == 8, "four or eight entries per lane");
+  constexpr unsigned ALL = (1u << E) - 1u;
+  constexpr uint32_t R = 32 * E;  // entries per round
   const unsigned lane = lane_id();
   uint32_t lane_hits = 0;
   next_val = NONE;
   if (x >= y) return;
-  uint32_t base = x & ~3u;
-  const uint4* src = reinterpret_cast<const uint4*>(P.adj + base) + lane;
-  const unsigned first = lane == 0 ? (0xFu << (x & 3u)) & 0xFu : 0xFu;  // entries >= x
-  unsigned head = first;
+  uint32_t base = x & ~(uint32_t)(E - 1);
+  const uint4* src = reinterpret_cast<const uint4*>(P.adj + base) + (E / 4) * lane;
+  unsigned head = lane == 0 ? (ALL << (x & (E - 1))) & ALL : ALL;  // entries >= x
+  uint4 nxt[E / 4];
+#pragma unroll
+  for (int q = 0; q < E / 4; ++q) nxt[q] = __ldg(src + q);
   while (true) {
-    const uint4 v = nxt;
-    const bool tail = base + 128 >= y;  // warp-uniform: this round reaches y
-    if (!tail) nxt = __ldg(src + 32);
-    const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+    uint32_t e[E];
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+      e[4 * q] = nxt[q].x;
+      e[4 * q + 1] = nxt[q].y;
+      e[4 * q + 2] = nxt[q].z;
+      e[4 * q + 3] = nxt[q].w;
+    }
+    const bool tail = base + R >= y;                                 // warp-uniform: this round reaches y
+    const bool fin = __any_sync(FULL, e[E - 1] >= segHi) || tail;   // warp-uniform: the visit ends here
+    if (!fin) {  // the next round, only when the visit goes on
+#pragma unroll
+      for (int q = 0; q < E / 4; ++q) nxt[q] = __ldg(src + 8 * E + q);
+    }
     unsigned hits = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < E; ++j) {
       const uint32_t b = e[j] - segLo;
       const uint32_t word = bm[min(b >> 5, seg_words)];
       hits |= (__funnelshift_r(word, word, b) & 1u) << j;
     }
     hits &= head;
-    const bool fin = __any_sync(FULL, v.w >= segHi) || tail;  // warp-uniform
     uint32_t stop = NONE;
     if (fin) {
-      const uint32_t idx0 = base + 4 * lane;
+      const uint32_t idx0 = base + E * lane;
       // entries below segHi, and those below x, are passed over
-      unsigned below = (unsigned)(e[0] < segHi) | ((unsigned)(e[1] < segHi) << 1) |
-                       ((unsigned)(e[2] < segHi) << 2) | ((unsigned)(e[3] < segHi) << 3);
-      below |= ~head & 0xFu;
-      const uint32_t j = (uint32_t)__ffs(~below) - 1u;  // 0..4
-      stop = min(__reduce_min_sync(FULL, j < 4 ? idx0 + j : NONE), y);
-      const uint32_t keep = idx0 < stop ? min(stop - idx0, 4u) : 0u;
+      unsigned below = ~head & ALL;
+#pragma unroll
+      for (int j = 0; j < E; ++j) below |= (unsigned)(e[j] < segHi) << j;
+      const uint32_t j = (uint32_t)__ffs(~below) - 1u;  // 0..E
+      stop = min(__reduce_min_sync(FULL, j < E ? idx0 + j : NONE), y);
+      const uint32_t keep = idx0 < stop ? min(stop - idx0, (uint32_t)E) : 0u;
       hits &= (1u << keep) - 1u;
-      const uint32_t rel = stop - base;  // 0..128
-      const uint32_t r3 = rel & 3u;
-      const uint32_t at = r3 == 0 ? e[0] : r3 == 1 ? e[1] : r3 == 2 ? e[2] : e[3];
-      const uint32_t val = __shfl_sync(FULL, at, (rel >> 2) & 31u);
+      const uint32_t rel = stop - base;  // 0..R
+      const uint32_t rj = rel & (E - 1);
+      uint32_t at = e[0];
+#pragma unroll
+      for (int q = 1; q < E; ++q)
+        if (rj == (uint32_t)q) at = e[q];
+      const uint32_t val = __shfl_sync(FULL, at, (rel / E) & 31u);
       next_val = stop < y ? val : NONE;
     }
-    seg_count_hits<MODE>(P, hits, e, lane_hits, hk, p, vj, tb);
+    seg_count_hits<MODE, E>(P, hits, e, lane_hits, hk, p, vj, tb);
     if (fin) {
       x = stop;
       break;
     }
-    head = 0xFu;
-    base += 128;
-    src += 32;
+    head = ALL;
+    base += R;
+    src += 8 * E;
   }
   found += lane_hits;
   if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += __reduce_add_sync(FULL, lane_hits);
@@ -590,7 +604,7 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
 template <int MODE>
 __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
                                                                uint32_t nh, uint32_t seg_bits,
-                                                               uint32_t seg_long,
+                                                               uint32_t seg_long, uint32_t seg_wide,
                                                                const uint32_t* __restrict__ bofs,
                                                                const uint32_t* __restrict__ bnd,
                                                                uint64_t bcap) {
@@ -722,8 +736,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         const uint32_t nlong = s_nlong;
         while (true) {
           uint32_t k, x, y;
-          uint4 v0;
-          seg_next_visit(P.adj, longs, nlong, &s_next, nextv, cur, endp, segHi, k, x, y, v0);
+          seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, k, x, y);
           if (k == NONE) break;
           uint32_t hk = ih[k], nv;
           uint32_t vj = 0;
@@ -733,7 +746,10 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
             tb = P.toff[P.wedge[i0 + k]];
           }
           const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-          seg_walk_item<MODE>(P, bm, seg_words, segLo, segHi, x, y, v0, hk, p, vj, tb, found, nv);
+          if (y - x >= seg_wide)  // long remaining list: rounds of 256 entries
+            seg_walk_item<MODE, 8>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+          else
+            seg_walk_item<MODE, 4>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
           if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
           __syncwarp();
           if (lane == 0) {
@@ -897,7 +913,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
-          P, task_ofs, nh, seg_bits, g->tune.seg_long, bofs, bcap ? bnd : nullptr, bcap);
+          P, task_ofs, nh, seg_bits, g->tune.seg_long, g->tune.seg_wide, bofs, bcap ? bnd : nullptr, bcap);
     AOT_TRY(last_launch());
   } else if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
@@ -1178,6 +1194,12 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
     for (uint32_t sl : longs) {
       aot_tuning t = cur;
       t.seg_long = sl;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t wides[] = {256u, 512u, 1024u, 4096u};
+    for (uint32_t sw : wides) {
+      aot_tuning t = cur;
+      t.seg_wide = sw;
       AOT_TRY(trial(t));
     }
     const uint32_t segs[] = {1572864u, 1048576u};

@@ -121,6 +121,7 @@ struct Tuning {
   int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)
   int hub_mode = 0;                 // 0: segmented shared-memory bitmap, 1: global bitmaps
   uint32_t seg_bits = 1536u * 1024u;  // ranks per shared-memory bitmap segment (hub_mode 0)
+  uint32_t seg_wide = 512;            // hub_mode 0: warp walks take rounds of 256 while this many entries remain
   uint32_t seg_long = 128;            // hub_mode 0: items this long walked warp-wide, shorter ones per thread
 };
 

@@ -321,9 +321,9 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
   L.ev0 = c.take<uint32_t>(ns); L.ev1 = c.take<uint32_t>(ns);
   L.perm = c.take<int32_t>(ns); L.rank = c.take<int32_t>(ns); L.degr = c.take<uint32_t>(ns);
   L.off = c.take<uint32_t>(ns + 1);
-  // padded: a warp's round of 128 entries that starts below m may read up to
-  // 127 entries past it (the entries there are masked, never counted)
-  L.adj = c.take<uint32_t>(Es + 128);
+  // padded: a warp's round of up to 256 entries that starts below m may read
+  // up to 255 entries past it (the entries there are masked, never counted)
+  L.adj = c.take<uint32_t>(Es + 256);
   L.outdeg = c.take<uint32_t>(ns);
   L.wofs = c.take<uint32_t>(ns + 1);
   L.items = c.take<uint32_t>(ns);

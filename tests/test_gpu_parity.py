@@ -117,6 +117,10 @@ def test_chunglu_full_parity():
     dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_mode=1, hub_bitmaps=7),  # global bitmaps
     dict(warp_max_outdeg=8, cta_max_outdeg=64, hub_mode=0, seg_bits=1024),  # many segments
     dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_mode=0, seg_bits=4096),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_wide=0),          # every warp walk in 256-entry rounds
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_wide=1 << 30),    # every warp walk in 128-entry rounds
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=1024, seg_long=0, seg_wide=0),  # all warp-wide
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=2048, seg_long=1 << 30),        # all per-thread
 ])
 def test_every_bin_gives_the_same_answer(tuning):
     n, s, d = gg.rmat_cfg(13, 7)
