@@ -563,8 +563,11 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
 }
 
 // One thread advances one short item through the segment [segLo, segHi):
-// four entries loaded at a time, stopping at the first entry >= segHi, whose
-// value is returned in nv.  Hits come out in order (listing ranks hk + i).
+// eight entries per step from two aligned 128-bit loads (base = x rounded
+// down to a multiple of 4; the entries below x are passed over), stopping at
+// the item's end y or at the first entry >= segHi, whose value is returned in
+// nv.  Hits come out in order (listing ranks hk + i).  The padded adjacency
+// array keeps the loads inside the allocation.
 template <int MODE>
 __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t* bm, uint32_t segLo,
                                                uint32_t segHi, uint32_t& x, uint32_t y,
@@ -573,20 +576,28 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
   const uint32_t width = segHi - segLo;
   nv = NONE;
   while (x < y) {
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = x + j < y ? __ldg(P.adj + x + j) : NONE;
-    uint32_t used = 0;
+    const uint32_t b0 = x & ~3u;
+    const uint4* q = reinterpret_cast<const uint4*>(P.adj + b0);
+    const uint4 lo = __ldg(q), hi = __ldg(q + 1);
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const uint32_t j0 = x & 3u;
+    uint32_t nx = b0 + 8;  // the cursor after these eight, unless the visit stops
     bool stop = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (stop) continue;
-      if (w[j] >= segHi) {  // also the padding past y (NONE)
+    for (int j = 0; j < 8; ++j) {
+      if (stop || (uint32_t)j < j0) continue;
+      const uint32_t idx = b0 + j;
+      if (idx >= y) {  // the item's end
         stop = true;
+        nx = y;
+        continue;
+      }
+      if (w[j] >= segHi) {  // the segment's end: resume here in a later segment
+        stop = true;
+        nx = idx;
         nv = w[j];
         continue;
       }
-      ++used;
       const uint32_t b = w[j] - segLo;
       if (b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) {
         ++found;
@@ -595,7 +606,7 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
         ++hk;
       }
     }
-    x += used;
+    x = nx;
     if (stop) break;
   }
   if (x >= y) nv = NONE;
