@@ -300,9 +300,11 @@ aot_status aot_set_default_tuning(const aot_tuning* t);
 aot_status aot_get_default_tuning(aot_tuning* t);
 
 /* Autotuner: coordinate search over the bin thresholds (CTA-hash cutoff,
- * warp cutoff), CTA size and bitmap segment width, timing each candidate on
- * this graph with CUDA events (best of reps) in mode 0 (count) or 1
- * (per-vertex count).  The fastest tuning is set on the graph and returned in
+ * warp cutoff), CTA size, the segmented walk's short/long and 128/256-entry
+ * thresholds and the bitmap segment width, timing each candidate on this
+ * graph with CUDA events (best of reps) in mode 0 (count) or 1 (per-vertex
+ * count); a candidate replaces the current tuning only when it is at least
+ * 1 % faster.  The chosen tuning is set on the graph and returned in
  * *best_out (may be NULL) with its time in *h_best_ms (may be NULL).
  * Synchronises s.  Results never change, only speed. */
 aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tuning* best_out,

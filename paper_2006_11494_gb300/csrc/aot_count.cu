@@ -1176,7 +1176,7 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       if (aot_graph_set_tuning(g, &cand, stream) != AOT_OK) return AOT_OK;  // skip invalid candidates
       float ms = 0.f;
       AOT_TRY(time_mode(g, mode, reps, s, &ms));
-      if (ms < best_ms) {
+      if (ms < 0.99f * best_ms) {  // a candidate must win by 1 %: near ties keep the current tuning
         best_ms = ms;
         cur = cand;
       }
