@@ -33,11 +33,18 @@ def aot():
 
 
 def edge_keys(s, d):
-    """Sorted distinct undirected edges of a raw pair list as uint64 keys."""
+    """Sorted distinct undirected edges of a raw pair list as uint64 keys
+    (sort, then drop repeats: far faster than np.unique at 2^28 keys)."""
     a = np.minimum(s, d).astype(np.uint64)
     b = np.maximum(s, d).astype(np.uint64)
     keep = a != b
-    return np.unique((a[keep] << np.uint64(32)) | b[keep])
+    k = np.sort((a[keep] << np.uint64(32)) | b[keep])
+    if len(k) == 0:
+        return k
+    first = np.empty(len(k), bool)
+    first[0] = True
+    np.not_equal(k[1:], k[:-1], out=first[1:])
+    return k[first]
 
 
 def eta_ranks(n, keys):
