@@ -46,7 +46,7 @@ MEASURED_TRAFFIC = {
         "bytes": 809978044672 + 5954697472,
         "sources": {
             "paper_2006_11494_gb300/csrc/aot_count.cu":
-                "52de2f8795e81be72b67ce9307412e58450a7d64e6bb640aeebb13273ac87ee1",
+                "f41ea22abecc212d6954106ecbcaf8d98fd34e764ff73444f091b690715aa77f",
             "paper_2006_11494_gb300/csrc/aot_kparams.cuh":
                 "231dda2e6ae44a42152841fae1136df9ff3f9499b0c0a802135686314e8628be",
             "paper_2006_11494_gb300/csrc/aot_internal.cuh":

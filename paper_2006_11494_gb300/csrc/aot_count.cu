@@ -350,8 +350,12 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
 // the bits of N+(p) in the segment, every warp advances its items' cursors
 // through the entries below the segment end (out-lists are sorted by eta, so
 // each walked entry is visited exactly once over all segments), then clears
-// the bits.  Items keep cursor, end and hit count in shared memory, so one
-// item's hits come out in ascending w order (the listing order).
+// the bits.  Items keep cursor, end, next walked value and hit count in
+// shared memory, so one item's hits come out in ascending w order (the
+// listing order).  Items shorter than seg_long entries are walked by one
+// thread each, longer ones by a warp in rounds of 128 entries (256 while at
+// least seg_wide entries remain).  Each pivot's segment bounds (positions in
+// N+(p)) are precomputed once per call by k_seg_bounds.
 constexpr int SEG_THREADS = 1024;
 constexpr uint32_t SEG_ITEMS = 1536;
 
