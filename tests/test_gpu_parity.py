@@ -121,6 +121,9 @@ def test_chunglu_full_parity():
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_wide=1 << 30),    # every warp walk in 128-entry rounds
     dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=1024, seg_long=0, seg_wide=0),  # all warp-wide
     dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=2048, seg_long=1 << 30),        # all per-thread
+    # every pivot on the bitmap path with 1024-rank segments: the per-pivot
+    # segment bounds do not fit their scratch, so each segment end is searched
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024),
 ])
 def test_every_bin_gives_the_same_answer(tuning):
     n, s, d = gg.rmat_cfg(13, 7)
@@ -164,6 +167,20 @@ def test_hub_wheel():
     n, s, d = gg.wheel(20000)  # hub deg+ 20000: beyond the shared-memory bins
     g, ref = check_full(n, s, d)
     assert g.info["max_outdeg"] == 20000
+
+
+def test_wheel_more_segments_than_shared_bounds():
+    """Wheel with a 600,000-vertex rim and 1024-rank segments: the hub's range
+    spans ~586 segments, more than the shared-memory bound table holds, so the
+    kernel searches each segment end.  Closed form as below."""
+    rim = 600_000
+    n, s, d = gg.wheel(rim)
+    g = gpu_graph(n, s, d)
+    g.set_tuning(seg_bits=1024)
+    assert g.count() == rim
+    T, t = g.count_per_vertex()
+    t = u64(t)
+    assert T == rim and t[0] == rim and np.all(t[1:] == 2)
 
 
 @pytest.mark.parametrize("hub_mode", [0, 1])
