@@ -58,6 +58,12 @@ MEASURED_TRAFFIC = {
 }
 
 
+def workload_name(scale, seed):
+    """The workload both arms name in their config."""
+    return ("R-MAT scale %d edge factor 16 (a,b,c,d)=(.57,.19,.19,.05) seed %d, "
+            "eta = degree non-increasing" % (scale, seed))
+
+
 def measured_traffic(kernel, scale, seed, tuning):
     """Bytes per launch from MEASURED_TRAFFIC when the sources and tuning still match, else None."""
     import hashlib
@@ -389,8 +395,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "R-MAT scale %d edge factor 16 (a,b,c,d)=(.57,.19,.19,.05) seed %d, "
-                               "eta = degree non-increasing" % (a.scale, a.seed),
+        "config": {"workload": workload_name(a.scale, a.seed),
                    "step": "aot_orient + aot_count_per_vertex (%s route)" % a.route,
                    "n": n, "generated_edges": E, "m": info["m"], "W": info["W"], "S": info["S"],
                    "max_outdeg": info["max_outdeg"], "triangles": T,
@@ -460,7 +465,10 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "R-MAT scale %d edge factor 16 seed %d (bounded prefix sample)" % (a.scale, a.seed)},
+        "config": {"workload": workload_name(a.scale, a.seed),
+                   "step": "oracle cleanup + per-vertex count of a bounded sample: the first 2^%d pairs "
+                           "of the same stream" % log2_sample,
+                   "n": n, "generated_edges": E, "m": m, "parallelism": "1 host core"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
