@@ -206,6 +206,7 @@ def bytes_per_kernel(info, bins, E, n):
 
     out["k_warp_pivots/vertex"] = (walk_bytes("warp"), 1)
     out["k_cta_pivots/vertex"] = (walk_bytes("cta"), 1)
+    out["k_warp_pivots_ctabin/vertex"] = (walk_bytes("cta"), 1)  # the CTA bin a warp per pivot
     out["k_seg_pivots/vertex"] = (walk_bytes("hub"), 1)
     out["k_hub_walk/vertex"] = (walk_bytes("hub") - 4 * bins["hub"]["staged"], None)
     return out

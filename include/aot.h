@@ -152,7 +152,8 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * entries walked by a warp (in rounds of 256 entries while at least seg_wide
  * entries remain, else of 128), shorter ones by a thread each; hub_mode 1:
  * global bitmaps of n bits, hub_bitmaps (1..32) hubs at a time, all CTAs
- * sharing their items.  cta_threads is a multiple of 32 in [64, 1024].
+ * sharing their items.  cta_threads is a multiple of 32 in [32, 1024]; 32
+ * runs the CTA bin a warp per pivot (its tables in the warp's shared memory).
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;

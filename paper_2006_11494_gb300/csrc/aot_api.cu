@@ -20,7 +20,7 @@ Tuning default_tuning() {
 }
 static bool tuning_valid(const aot_tuning* t) {
   return !(t->warp_max_outdeg > 64 || t->cta_max_outdeg > 8192 ||
-           t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 64 || t->cta_threads > 1024 ||
+           t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 32 || t->cta_threads > 1024 ||
            (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
            t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
            (t->seg_bits & 31) || t->seg_long > (1u << 30) || t->seg_wide > (1u << 30));

@@ -171,18 +171,23 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
 }
 
 // ------------------------------------------------------------ warp kernel
-constexpr int WARP_TS = 128;  // slots per warp table (deg+ <= 64)
+constexpr int WARP_TS = 128;  // slots per warp table of the warp bin (deg+ <= 64)
 
+// A warp per pivot, its hash table (ts_max slots, plus as many hit counters
+// in per-vertex mode) in the warp's share of dynamic shared memory; pivots
+// come from queue q.  Used
+// for the warp bin and, with cta_threads = 32, for the CTA bin: no CTA-wide
+// barrier, so a pivot with long items holds up only its own warp.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_warp_pivots(KParams P) {
-  __shared__ uint32_t sm[256 / 32][2 * WARP_TS];
+__global__ void __launch_bounds__(256) k_warp_pivots(KParams P, uint32_t ts_max, int q) {
+  extern __shared__ uint32_t wp_sm[];
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-  uint32_t* tab = sm[wid];
-  uint32_t* cnt = sm[wid] + WARP_TS;
+  uint32_t* tab = wp_sm + (size_t)wid * (MODE == M_VERTEX ? 2 : 1) * ts_max;
+  uint32_t* cnt = tab + ts_max;  // per-vertex mode only
   uint64_t found = 0;
   while (true) {
     uint32_t idx = 0;
-    if (lane == 0) idx = atomicAdd(&P.dev->counters[Q_WARP], 1u);
+    if (lane == 0) idx = atomicAdd(&P.dev->counters[q], 1u);
     idx = __shfl_sync(FULL, idx, 0);
     if (idx >= P.num_pivots) break;
     const uint32_t p = P.pivots[idx];
@@ -829,6 +834,7 @@ static const char* const kWarpNames[5] = AOT_MODE_NAMES(k_warp_pivots);
 static const char* const kCtaNames[5] = AOT_MODE_NAMES(k_cta_pivots);
 static const char* const kHubNames[5] = AOT_MODE_NAMES(k_hub_walk);
 static const char* const kSegNames[5] = AOT_MODE_NAMES(k_seg_pivots);
+static const char* const kWarpCtaNames[5] = AOT_MODE_NAMES(k_warp_pivots_ctabin);  // the CTA bin a warp per pivot
 template <int MODE>
 static const char* mode_name(const char* base) {
   if (base[2] == 'w') return kWarpNames[MODE];
@@ -852,23 +858,52 @@ template <int MODE>
 static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
   const uint32_t nw = g->bin_count[BIN_WARP], nc = g->bin_count[BIN_CTA], nh = g->bin_count[BIN_HUB];
   const int sms = sm_count();
+  // a warp per pivot with ts_max-slot tables; warps per CTA chosen (8, 4, 2
+  // or 1) for the most resident warps
+  static size_t warp_attr[5] = {0, 0, 0, 0, 0};
+  auto launch_warps = [&](uint32_t count, uint32_t ts_max, int q, const char* name) -> aot_status {
+    const size_t per_warp = (size_t)(MODE == M_VERTEX ? 2 : 1) * ts_max * sizeof(uint32_t);
+    const size_t smem_cap = 227 * 1024;
+    const size_t attr = per_warp * 8 < smem_cap ? per_warp * 8 : smem_cap;
+    if (attr > 48 * 1024 && warp_attr[MODE] < attr) {
+      AOT_CUDA(cudaFuncSetAttribute(k_warp_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)attr));
+      warp_attr[MODE] = attr;
+    }
+    int warps_per_block = 1, per_sm = 0, best = -1;
+    for (int w = 8; w >= 1; w >>= 1) {
+      const size_t sm_bytes = (size_t)w * per_warp;
+      if (sm_bytes > attr && sm_bytes > 48 * 1024) continue;
+      int b = 0;
+      AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_warp_pivots<MODE>, 32 * w, sm_bytes));
+      if (b * w > best) {
+        best = b * w;
+        warps_per_block = w;
+        per_sm = b;
+      }
+    }
+    const size_t smem = (size_t)warps_per_block * per_warp;
+    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = ((int64_t)count + warps_per_block - 1) / warps_per_block;
+    if (grid > need) grid = need;
+    AOT_KERNEL(name, s)
+      k_warp_pivots<MODE><<<(unsigned)grid, 32 * warps_per_block, smem, s>>>(P, ts_max, q);
+    return last_launch();
+  };
   if (nw) {
     P.pivots = g->bin_pivots;
     P.num_pivots = nw;
-    int per_sm = 0;
-    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_pivots<MODE>, 256, 0));
-    int64_t grid = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    int64_t need = (nw + 7) / 8;
-    if (grid > need) grid = need;
-    AOT_KERNEL(mode_name<MODE>("k_warp_pivots"), s)
-      k_warp_pivots<MODE><<<(unsigned)grid, 256, 0, s>>>(P);
-    AOT_TRY(last_launch());
+    AOT_TRY(launch_warps(nw, WARP_TS, Q_WARP, mode_name<MODE>("k_warp_pivots")));
   }
-  if (nc) {
+  uint32_t cta_ts = 64;  // table slots of the CTA bin: a power of two >= 2 cta_max
+  while (cta_ts < 2 * g->binned_cta_max) cta_ts <<= 1;
+  if (nc && g->tune.cta_threads == 32) {  // the CTA bin a warp per pivot
     P.pivots = g->bin_pivots + nw;
     P.num_pivots = nc;
-    uint32_t ts_max = 64;
-    while (ts_max < 2 * g->binned_cta_max) ts_max <<= 1;
+    AOT_TRY(launch_warps(nc, cta_ts, Q_CTA, kWarpCtaNames[MODE]));
+  } else if (nc) {
+    P.pivots = g->bin_pivots + nw;
+    P.num_pivots = nc;
+    const uint32_t ts_max = cta_ts;
     size_t smem = (size_t)ts_max * 2 * sizeof(uint32_t);
     static size_t attr_done[5] = {0, 0, 0, 0, 0};
     if (attr_done[MODE] < smem) {
@@ -1193,7 +1228,7 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       t.warp_max_outdeg = c < t.warp_max_outdeg ? c : t.warp_max_outdeg;
       AOT_TRY(trial(t));
     }
-    const int threads[] = {256, 512, 1024};
+    const int threads[] = {32, 256, 512, 1024};  // 32: the CTA bin a warp per pivot
     for (int th : threads) {
       aot_tuning t = cur;
       t.cta_threads = th;

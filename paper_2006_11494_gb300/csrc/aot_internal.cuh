@@ -116,7 +116,7 @@ enum Bin { BIN_WARP = 0, BIN_CTA = 1, BIN_HUB = 2, NUM_BINS = 3 };
 struct Tuning {
   uint32_t warp_max_outdeg = 64;    // BIN_WARP: 1..warp_max (table 2*pow2 slots)
   uint32_t cta_max_outdeg = 512;    // BIN_CTA: ..cta_max (smem hash)
-  int cta_threads = 256;
+  int cta_threads = 32;              // 32: the CTA bin a warp per pivot
   int warp_cta_threads = 256;
   int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)
   int hub_mode = 0;                 // 0: segmented shared-memory bitmap, 1: global bitmaps

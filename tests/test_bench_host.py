@@ -1,37 +1,45 @@
-"""Host logic of bench.py: the measured DRAM traffic is reported only for the
-kernel sources and the tuning it was captured with."""
-import os
-import shutil
+"""Host logic of bench.py: a measured DRAM traffic figure is reported only for
+the kernel sources and the tuning it was captured with (checked here on
+stand-in source files, so the test does not depend on the real kernels)."""
+import hashlib
 
 import bench
 
 KEY = ("k_seg_pivots/vertex", 24, 3)
+TUNING = {"cta_max_outdeg": 512, "seg_long": 128}
 
 
-def _copy_sources(tmp_path):
-    entry = bench.MEASURED_TRAFFIC[KEY]
-    for rel in entry["sources"]:
-        dst = tmp_path / rel
-        os.makedirs(dst.parent, exist_ok=True)
-        shutil.copyfile(os.path.join(bench.ROOT, rel), dst)
+def _entry(tmp_path, monkeypatch):
+    sources = {}
+    for rel, text in (("src/a.cu", b"kernel a\n"), ("src/b.cuh", b"header b\n")):
+        path = tmp_path / rel
+        path.parent.mkdir(parents=True, exist_ok=True)
+        path.write_bytes(text)
+        sources[rel] = hashlib.sha256(text).hexdigest()
+    entry = {"bytes": 123456789, "sources": sources, "tuning": dict(TUNING)}
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {KEY: entry})
     return entry
 
 
 def test_traffic_needs_the_captured_tuning(tmp_path, monkeypatch):
-    entry = _copy_sources(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic(*KEY, dict(entry["tuning"])) == entry["bytes"]
-    other = dict(entry["tuning"], seg_long=entry["tuning"]["seg_long"] * 2)
-    assert bench.measured_traffic(*KEY, other) is None
+    entry = _entry(tmp_path, monkeypatch)
+    assert bench.measured_traffic(*KEY, dict(TUNING)) == entry["bytes"]
+    assert bench.measured_traffic(*KEY, dict(TUNING, seg_long=256)) is None
     assert bench.measured_traffic(*KEY, None) is None
-    assert bench.measured_traffic("k_cta_pivots/vertex", 24, 3, dict(entry["tuning"])) is None
-    assert bench.measured_traffic(KEY[0], 22, 3, dict(entry["tuning"])) is None
+    assert bench.measured_traffic("k_cta_pivots/vertex", 24, 3, dict(TUNING)) is None
+    assert bench.measured_traffic(KEY[0], 22, 3, dict(TUNING)) is None
 
 
 def test_traffic_is_dropped_when_a_kernel_source_changes(tmp_path, monkeypatch):
-    entry = _copy_sources(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    rel = next(iter(entry["sources"]))
-    with open(tmp_path / rel, "ab") as f:
+    _entry(tmp_path, monkeypatch)
+    with open(tmp_path / "src/a.cu", "ab") as f:
         f.write(b"\n")
-    assert bench.measured_traffic(*KEY, dict(entry["tuning"])) is None
+    assert bench.measured_traffic(*KEY, dict(TUNING)) is None
+
+
+def test_recorded_entry_names_existing_sources():
+    for (kernel, scale, seed), e in bench.MEASURED_TRAFFIC.items():
+        assert e["bytes"] > 0 and e["tuning"]
+        for rel in e["sources"]:
+            assert (bench.os.path.exists(bench.os.path.join(bench.ROOT, rel))), rel

@@ -113,6 +113,8 @@ def test_chunglu_full_parity():
     dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_bitmaps=32),
     dict(warp_max_outdeg=64, cta_max_outdeg=64),                   # warp + hub
     dict(warp_max_outdeg=1, cta_max_outdeg=8192, cta_threads=128),  # almost all CTA
+    dict(warp_max_outdeg=1, cta_max_outdeg=8192, cta_threads=32),   # the CTA bin a warp per pivot
+    dict(warp_max_outdeg=16, cta_max_outdeg=512, cta_threads=32),
     dict(warp_max_outdeg=16, cta_max_outdeg=256, cta_threads=1024, hub_bitmaps=3),
     dict(warp_max_outdeg=0, cta_max_outdeg=0, hub_mode=1, hub_bitmaps=7),  # global bitmaps
     dict(warp_max_outdeg=8, cta_max_outdeg=64, hub_mode=0, seg_bits=1024),  # many segments
