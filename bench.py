@@ -43,16 +43,16 @@ FALLBACK_HBM_GBS = 6800.0
 # sources and tuning it was taken with: any change reports null.
 MEASURED_TRAFFIC = {
     ("k_seg_pivots/vertex", 24, 3): {
-        "bytes": 809978044672 + 5954697472,
+        "bytes": 809835580160 + 5946050816,
         "sources": {
             "paper_2006_11494_gb300/csrc/aot_count.cu":
-                "f41ea22abecc212d6954106ecbcaf8d98fd34e764ff73444f091b690715aa77f",
+                "7137453b14fc3136d50d29f8a5112209dc328e069ee653117cbf66ce5411244a",
             "paper_2006_11494_gb300/csrc/aot_kparams.cuh":
                 "231dda2e6ae44a42152841fae1136df9ff3f9499b0c0a802135686314e8628be",
             "paper_2006_11494_gb300/csrc/aot_internal.cuh":
-                "9ab432fd08de5a226882df3d30830b92732484538bcfcb4c2577133a847dde46",
+                "fee74f7c4b88cbf01768907719351d7d20096fb3452c5644718cc013d569c014",
         },
-        "tuning": {"warp_max_outdeg": 64, "cta_max_outdeg": 512, "cta_threads": 256, "hub_bitmaps": 32,
+        "tuning": {"warp_max_outdeg": 64, "cta_max_outdeg": 512, "cta_threads": 32, "hub_bitmaps": 32,
                    "hub_mode": 0, "seg_bits": 1572864, "seg_long": 128, "seg_wide": 512},
     },
 }
