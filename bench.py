@@ -15,7 +15,7 @@ region.
 --impl reference times the CPU oracle (the slow reference program of this
 project) on a bounded prefix sample of the same edge stream.
 Under torchrun (N > 1) every rank runs an independent replica of the
-workload (the graph does not shard in this build: replicas only).
+workload (the graph is not sharded: replicas only).
 """
 from __future__ import annotations
 
@@ -38,9 +38,9 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic per launch of the dominant kernel on the default workload, from
 # one ncu capture of this command's timed launch (dram__bytes_read.sum +
-# dram__bytes_write.sum, a one-pass metric set; summary and command in
-# profiles/k_seg_pivots_rmat_s24_dram.md).  It stands only for the kernel
-# sources and tuning it was taken with: any change reports null.
+# dram__bytes_write.sum, a one-pass metric set, taken right after the same
+# command exited 0 without ncu).  It stands only for the kernel sources and
+# tuning it was taken with: any change reports null.
 MEASURED_TRAFFIC = {
     ("k_seg_pivots/vertex", 24, 3): {
         "bytes": 809835580160 + 5946050816,
@@ -187,7 +187,10 @@ class ClockSampler:
 
 # ------------------------------------------------------- algorithmic bytes
 def bytes_per_kernel(info, bins, E, n):
-    """Algorithmic HBM bytes of one step, per kernel family."""
+    """Algorithmic HBM bytes of one step, per kernel family: each radix pass
+    reads (histogram) and moves (scatter) every key once; an intersection bin
+    stages N+(p) of its pivots, reads their offsets and their items' walk
+    ranges and walked vertices, and every walked adjacency entry once."""
     m, bits = info["m"], max(1, math.ceil(math.log2(max(n, 2))))
     passes_keys = math.ceil(2 * bits / 8)
     passes_eta = math.ceil(bits / 8)

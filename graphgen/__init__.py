@@ -11,11 +11,11 @@ Workload recipes (the synthetic stand-ins for the paper's real graphs, whose
 shape is described in its Table 2: average degree 4-53, maximum degree
 10^3.5-10^6.5):
 
-* ``er_c1``      Erdos-Renyi, n = 16384, 262144 uniform pairs, seed 1
+* ``er_16k``     Erdos-Renyi, n = 16384, 262144 uniform pairs, seed 1
 * ``rmat(s)``    R-MAT scale s, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05),
                  ids relabelled by a seeded permutation
 * ``chunglu``    Chung-Lu, weights ~ (i+1)^(-1/(gamma-1)), mean degree d
-* ``batch_c5``   4096 Chung-Lu graphs, n log-uniform in [256, 65536], mean
+* ``batch``      4096 Chung-Lu graphs, n log-uniform in [256, 65536], mean
                  degree uniform in [4, 64], gamma = 2.5, per-graph seeds
 """
 from __future__ import annotations
@@ -128,7 +128,7 @@ def draw(seed: int, stream: int, k: int) -> int:
 
 
 # ----------------------------------------------------------------- recipes
-def er_c1():
+def er_16k():
     """Erdos-Renyi, n = 16384, 262144 uniform pairs, seed 1."""
     n = 16384
     s, d = er(n, 262144, seed=1)

@@ -1,7 +1,7 @@
 """ORACLE for the learned router -- test infrastructure only (only tests/,
 __graft_entry__.smoke() and bench.py's cpu_baseline leg may import it).
 
-The paper has no learned component.  The router is this build's addition:
+The paper has no learned component.  The router is an addition to the method:
 an 8 -> 64 -> 64 -> 3 perceptron (ReLU after the two hidden layers) that
 predicts, for one oriented edge, the standardised log cost of each of three
 intersection variants.  Its features are defined on the oriented graph of

@@ -108,7 +108,7 @@ def test_batch_rejects_bad_input(aot):
     assert list(tri) == [4, 10]
 
 
-def test_config5_full_batch(aot):
+def test_batch_of_4096_chunglu_graphs(aot):
     """4096 Chung-Lu graphs (n log-uniform in [256, 65536], mean degree
     uniform in [4, 64], gamma 2.5): every graph's per-vertex counts sum to 3T;
     24 graphs (the largest ones and a seeded sample) against the oracle."""

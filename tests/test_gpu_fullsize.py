@@ -1,16 +1,16 @@
-"""Full-size configurations, checked on sampled outputs the oracle computes one
-by one and on properties that hold at any size.
+"""Full-size workloads, checked on sampled outputs the oracle computes one by
+one and on properties that hold at any size.
 
-config 2  R-MAT scale 20: m and W against the oracle; t(v) of sampled
-          vertices (oracle, edges among N(v)); count = per-vertex total / 3 =
-          listed triangles; the full list in canonical order (every triangle
-          checked on the GPU against an eta computed here from the raw edges);
-          sampled triangles are triangles of the input.
-config 3  R-MAT scale 24: the same with the list streamed in chunks of 2^28
-          triangles and t(v) sampled straight from the raw edge list.
-config 4  R-MAT scale 27 and Chung-Lu 2^27 (gamma 2.1, mean degree 32):
-          count and per-vertex counts; sampled t(v) from the raw edge list;
-          the learned route and the global-bitmap hub path agree.
+* R-MAT scale 20: m and W against the oracle; t(v) of sampled vertices
+  (oracle, edges among N(v)); count = per-vertex total / 3 = listed
+  triangles; the full list in canonical order (every triangle checked on the
+  GPU against an eta computed here from the raw edges); sampled triangles
+  are triangles of the input.
+* R-MAT scale 24: the same with the list streamed in chunks of 2^28
+  triangles and t(v) sampled straight from the raw edge list.
+* R-MAT scale 27 and Chung-Lu 2^27 (gamma 2.1, mean degree 32): count and
+  per-vertex counts; sampled t(v) from the raw edge list; the learned route
+  and the global-bitmap hub path agree.
 """
 import numpy as np
 import pytest
@@ -117,7 +117,7 @@ def orient(aot, n, s, d, flags=0):
     return aot.OrientedGraph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n, flags)
 
 
-def test_config2_rmat20(aot):
+def test_rmat20_full_size(aot):
     rng = np.random.default_rng(20)
     n, s, d = gg.rmat_cfg(20, 2)
     ref = oracle.Graph(n, s, d)
@@ -138,7 +138,7 @@ def test_config2_rmat20(aot):
     assert stream_list(aot, g, 1 << 26, rank, keys, 2000, rng) == T
 
 
-def test_config3_rmat24_streamed_listing(aot):
+def test_rmat24_streamed_listing(aot):
     rng = np.random.default_rng(24)
     n, s, d = gg.rmat_cfg(24, 3)
     g = orient(aot, n, s, d)
@@ -159,7 +159,7 @@ def test_config3_rmat24_streamed_listing(aot):
 
 
 @pytest.mark.parametrize("which", ["rmat27", "chunglu27"])
-def test_config4_billion_edges(aot, which):
+def test_two_billion_pair_graphs(aot, which):
     import torch
     from paper_2006_11494_gb300 import router
     rng = np.random.default_rng(27)

@@ -75,9 +75,9 @@ def test_closed_forms(case):
     check_full(n, s, d)
 
 
-# --------------------------------------------------------- config 1 (ER)
-def test_er_c1_full_parity_and_orientation():
-    n, s, d = gg.er_c1()
+# ------------------------------------------- ER, n = 16384, 262144 pairs
+def test_er_16k_full_parity_and_orientation():
+    n, s, d = gg.er_16k()
     g, ref = check_full(n, s, d)
     rank, perm, off, adj = ref.orient(oracle.ORDER_DESC)
     ex = g.export()

@@ -51,7 +51,7 @@ def static_call(aot, src, dst, n, with_counts=True):
 
 def test_static_matches_regular_on_two_calls_in_a_row(aot):
     import torch
-    cases = [gg.er_c1(), gg.rmat_cfg(12, 3)]
+    cases = [gg.er_16k(), gg.rmat_cfg(12, 3)]
     for n, s, d in cases:  # second call reuses the array the first one left behind
         src = torch.from_numpy(s).cuda()
         dst = torch.from_numpy(d).cuda()
