@@ -25,6 +25,10 @@ namespace aot {
 constexpr int MLP_IN = 8, MLP_H = 64, MLP_OUT = 3;
 constexpr int P_W1 = 0, P_B1 = 512, P_W2 = 576, P_B2 = 4672, P_W3 = 4736, P_B3 = 4928;
 constexpr int P_TOTAL = 4931;
+static_assert(P_B1 == P_W1 + MLP_H * MLP_IN && P_W2 == P_B1 + MLP_H && P_B2 == P_W2 + MLP_H * MLP_H &&
+                  P_W3 == P_B2 + MLP_H && P_B3 == P_W3 + MLP_OUT * MLP_H && P_TOTAL == P_B3 + MLP_OUT &&
+                  P_TOTAL == AOT_MLP_PARAMS,
+              "parameter layout W1[64][8], b1[64], W2[64][64], b2[64], W3[3][64], b3[3]");
 constexpr size_t MO_PARAMS = 128;  // byte offset of the bf16 parameters in a model
 
 struct ModelView {
