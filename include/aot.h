@@ -144,16 +144,18 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
 
 /* Launch tuning of the intersection kernels.  Pivots are binned by deg+:
  * deg+ <= warp_max_outdeg -> one warp per pivot (hash table in the warp's
- * shared memory; warp_max_outdeg <= 64), deg+ <= cta_max_outdeg -> one CTA
- * per pivot (shared-memory hash table; cta_max_outdeg <= 8192), larger ->
- * hub path.  hub_mode 0: a shared-memory bitmap over eta ranks, swept one
+ * shared memory; warp_max_outdeg <= 64), deg+ <= cta_max_outdeg -> the CTA
+ * bin (shared-memory hash table; cta_max_outdeg <= 8192; a CTA of
+ * cta_threads threads per pivot, or a warp per pivot when cta_threads is
+ * 32), larger -> hub path.  hub_mode 0: a shared-memory bitmap over eta ranks, swept one
  * segment of seg_bits ranks at a time (a multiple of 32 in [1024, 1572864])
  * by a CTA per (pivot, block of 1536 items), items with at least seg_long
  * entries walked by a warp (in rounds of 256 entries while at least seg_wide
  * entries remain, else of 128), shorter ones by a thread each; hub_mode 1:
  * global bitmaps of n bits, hub_bitmaps (1..32) hubs at a time, all CTAs
- * sharing their items.  cta_threads is a multiple of 32 in [32, 1024]; 32
- * runs the CTA bin a warp per pivot (its tables in the warp's shared memory).
+ * sharing their items.  cta_threads is a multiple of 32 in [32, 1024].
+ * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
+ * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;

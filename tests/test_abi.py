@@ -96,3 +96,11 @@ def test_product_does_not_import_oracle():
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "import paper_2006_11494_gb300" not in text and "aot.h" not in text, f
             assert "libaot" not in text, f
+
+
+def test_documented_default_tuning_is_the_built_in_one(aot):
+    text = open(os.path.join(ROOT, "include", "aot.h")).read()
+    m = re.search(r"Built-in defaults:(.*?)\.\s*\n", text, flags=re.S)
+    assert m, "the header lists the built-in defaults"
+    doc = dict((k, int(v)) for k, v in re.findall(r"(\w+) (\d+)", m.group(1).replace("*", " ")))
+    assert doc == aot.aot_get_default_tuning().as_dict()
