@@ -318,6 +318,7 @@ def run_ours(a):
         from paper_2006_11494_gb300 import router as rt
         count_only_ms = phase_ms(lambda: aot.aot_count(h, aot.ROUTE_PLAIN, stream), a.steps)
         extras["count_only_ms"] = count_only_ms
+        extras["count_only_hbm_frac"] = count_phase_bytes(info, n) / (count_only_ms / 1e3) / 1e9 / measured_peak()[0]
         model = rt.load()
         if model is not None:
             aot.aot_graph_set_router(h, model)
