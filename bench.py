@@ -35,6 +35,10 @@ METRIC = "oriented edges/s & triangles/s at R-MAT s24, learned vs plain; HBM roo
 UNIT = "oriented edges/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# The oracle (cleanup + parallel per-vertex count on every host core) runs on
+# the first 2^CPU_SAMPLE_LOG2 pairs of the benchmark's edge stream: the full
+# 2^28-pair graph takes minutes of host time, this prefix tens of seconds.
+CPU_SAMPLE_LOG2 = 26
 
 # DRAM traffic per launch of the dominant kernel on the default workload, from
 # one ncu capture of this command's timed launch (dram__bytes_read.sum +
@@ -64,6 +68,30 @@ def workload_name(scale, seed):
             "eta = degree non-increasing" % (scale, seed))
 
 
+def workload_config(scale, seed):
+    """The config both arms print (identical, so that the arms compare)."""
+    return {"workload": workload_name(scale, seed), "n": 1 << scale, "generated_edges": 16 << scale,
+            "l2": "inputs larger than L2 (2 GB edge list, 129 MB L2)"}
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def measured_traffic(kernel, scale, seed, tuning):
     """Bytes per launch from MEASURED_TRAFFIC when the sources and tuning still match, else None."""
     import hashlib
@@ -88,8 +116,10 @@ def parse():
     ap.add_argument("--route", default="plain", choices=["plain", "learned"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-log2", type=int, default=23,
-                    help="log2 of the edge-stream prefix the CPU baseline runs on")
+    ap.add_argument("--cpu-sample-log2", type=int, default=CPU_SAMPLE_LOG2,
+                    help="log2 of the edge-stream prefix the CPU baseline and the reference arm run on")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the CPU baseline and the reference arm (0: all cores)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (built-in tuning)")
     ap.add_argument("--tuning", default=None,
                     help="JSON object of aot_tuning fields to use instead of autotuning")
@@ -282,9 +312,9 @@ def run_ours(a):
     torch.cuda.synchronize()
     T = int(counts.sum().item()) // 3
 
-    # timed region: K steps, inputs resident in HBM (2 GB edge list > L2)
+    # timed region: K steps, inputs resident in HBM (2 GB edge list > L2),
+    # no per-launch events
     l0 = aot.aot_kernel_launches()
-    aot.aot_profile_begin()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
@@ -295,9 +325,20 @@ def run_ours(a):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    prof = aot.aot_profile_end()
     launches = aot.aot_kernel_launches() - l0
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
+    # the same K steps again with a pair of CUDA events around every launch
+    # (on its stream): per-kernel durations for the roofline
+    aot.aot_profile_begin()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p0.record(stream)
+    for _ in range(a.steps):
+        aot.aot_graph_destroy(step(src, dst))
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof = aot.aot_profile_end()
+    profiled_ms = p0.elapsed_time(p1) / a.steps
 
     # count phase alone, for context: plain route, learned route, count mode
     def phase_ms(fn, reps):
@@ -393,19 +434,20 @@ def run_ours(a):
 
     cpu = None
     if not a.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(a.scale, a.seed, a.cpu_sample_log2, h_src.numpy(), h_dst.numpy())
+        cpu = cpu_baseline(a.scale, a.seed, a.cpu_sample_log2, a.cpu_threads, h_src.numpy(),
+                           h_dst.numpy())
 
     value = replica_value(info["m"], ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_name(a.scale, a.seed),
-                   "step": "aot_orient + aot_count_per_vertex (%s route)" % a.route,
-                   "n": n, "generated_edges": E, "m": info["m"], "W": info["W"], "S": info["S"],
-                   "max_outdeg": info["max_outdeg"], "triangles": T,
-                   "l2": "inputs larger than L2 (2 GB edge list, 129 MB L2)",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "config": workload_config(a.scale, a.seed),
+        "parallelism": "replicas" if world > 1 else "1 GPU",
+        "step": "aot_orient + aot_count_per_vertex (%s route)" % a.route,
+        "graph": {"m": info["m"], "W": info["W"], "S": info["S"], "max_outdeg": info["max_outdeg"],
+                  "triangles": T},
+        "profiled_ms_per_step": profiled_ms,
         "triangles_per_s": world * T / (ms / 1e3),
         "count_phase": {"ms": count_ms, "oriented_edges_per_s": info["m"] / (count_ms / 1e3),
                         "triangles_per_s": T / (count_ms / 1e3), "probes_per_s": info["W"] / (count_ms / 1e3),
@@ -425,56 +467,63 @@ def run_ours(a):
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_baseline(scale, seed, log2_sample, src_np, dst_np):
-    """The oracle, as it stands, on a prefix of the same edge stream."""
+def oracle_step(n, src, dst, threads):
+    """One step of the oracle as it stands: cleanup (og_new_par) and the
+    parallel per-vertex count (og_count_par) on `threads` host threads."""
+    import oracle
+    g = oracle.Graph(n, src, dst, threads=threads)
+    T, _ = g.count_per_vertex_par(threads)
+    return g.m, T
+
+
+def sample_text(scale, log2_sample, m, T, cores):
+    return ("first 2^%d of the %d generated pairs of the same R-MAT stream (m=%d oriented edges, "
+            "T=%d; sparser in triangles than the full graph): cleanup + per-vertex count, "
+            "%d host threads (%s)" % (log2_sample, 16 << scale, m, T, cores, cpu_model()))
+
+
+def cpu_baseline(scale, seed, log2_sample, threads, src_np, dst_np):
+    """The oracle, as it stands, on a prefix of the same edge stream, on every
+    host core."""
     import oracle
     n = 1 << scale
     E = 1 << log2_sample
+    cores = oracle.host_threads(threads)
     t0 = time.perf_counter()
-    g = oracle.Graph(n, src_np[:E], dst_np[:E])
-    T, _ = g.count_per_vertex()
+    m, T = oracle_step(n, src_np[:E], dst_np[:E], cores)
     dt = time.perf_counter() - t0
-    return {"value": g.m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first 2^%d of the %d generated pairs of the same R-MAT stream "
-                      "(m=%d, T=%d; far sparser in triangles than the full graph); cleanup + "
-                      "per-vertex count, %.1f s" % (log2_sample, 16 << scale, g.m, T, dt)}
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": sample_text(scale, log2_sample, m, T, cores)}
 
 
 def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
     import graphgen as gg
     import oracle
-    log2_sample = 21
+    log2_sample = a.cpu_sample_log2
     E = 1 << log2_sample
     n = 1 << a.scale
+    cores = oracle.host_threads(a.cpu_threads)
     # the first E pairs of the same stream (pairs are drawn independently)
     src, dst = gg.rmat(a.scale, 16, a.seed, num_edges=E)
-
-    def step():
-        g = oracle.Graph(n, src, dst)
-        g.count_per_vertex()
-        return g.m
     for _ in range(a.warmup):
-        step()
+        oracle_step(n, src, dst, cores)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        m = step()
+        m, T = oracle_step(n, src, dst, cores)
     dt = (time.perf_counter() - t0) / a.steps
     v = m / dt
-    sample = "first 2^%d generated pairs of the R-MAT scale-%d stream (m=%d); cleanup + per-vertex count" % (
-        log2_sample, a.scale, m)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_name(a.scale, a.seed),
-                   "step": "oracle cleanup + per-vertex count of a bounded sample: the first 2^%d pairs "
-                           "of the same stream" % log2_sample,
-                   "n": n, "generated_edges": E, "m": m, "parallelism": "1 host core"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": workload_config(a.scale, a.seed),
+        "parallelism": "%d host threads" % cores,
+        "step": "oracle cleanup + per-vertex count of a bounded sample of the workload",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample_text(a.scale, log2_sample, m, T, cores)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -289,9 +289,12 @@ aot_status aot_profile_end(aot_profile_entry* out, int32_t cap, int32_t* count);
  * 42.0 MB and are rejected).
  * The first call on a device (run with that device current) looks up the
  * array's device address and caches it: make that first call before any
- * stream capture.  All calls share the array, which keeps the last call's
- * contents (each call re-initialises what must start at zero): calls that
- * overlap on the GPU race, so serialise them. */
+ * stream capture.  The cached address does not survive cudaDeviceReset: do
+ * not call this entry point on a device after resetting it.  All calls share
+ * the array, which keeps the last call's contents (each call re-initialises
+ * what must start at zero): calls that overlap on the GPU race, so serialise
+ * them.  A call that fails after queuing kernels synchronises s before it
+ * returns. */
 #define AOT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 aot_status aot_count_per_vertex_static(const int32_t* d_src, const int32_t* d_dst,
                                        int64_t num_edges, int32_t num_vertices,

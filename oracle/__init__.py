@@ -30,11 +30,12 @@ OK, ERR_ARG, ERR_RANGE, ERR_NOMEM = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (plain -O2, no OpenMP)."""
+    """Compile liboracle.so with gcc (plain -O2; OpenMP for the *_par paths)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC,
+                               "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -74,6 +75,15 @@ def _L():
         lib.og_stream_vertex_counts.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P,
                                                 ctypes.c_int32, P, P]
         lib.og_stream_vertex_counts.restype = ctypes.c_int
+        lib.og_threads.argtypes = [ctypes.c_int]
+        lib.og_threads.restype = ctypes.c_int
+        lib.og_new_par.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int]
+        lib.og_new_par.restype = P
+        lib.og_count_par.argtypes = [P, P, ctypes.c_int]
+        lib.og_count_par.restype = ctypes.c_uint64
+        lib.og_list_canonical_par.argtypes = [P, ctypes.c_int, P, ctypes.c_uint64, ctypes.c_int]
+        lib.og_list_canonical_par.restype = ctypes.c_uint64
         _lib = lib
     return _lib
 
@@ -93,13 +103,19 @@ class Graph:
     """The cleaned simple graph of an undirected edge list (loops dropped,
     duplicate and reversed pairs merged, ids checked against [0, n))."""
 
-    def __init__(self, n: int, src, dst):
+    def __init__(self, n: int, src, dst, threads: int = None):
+        """threads=None: the serial og_new; an int: og_new_par with that many
+        threads (0 = all host cores)."""
         src, dst = _i32(src), _i32(dst)
         if src.shape != dst.shape:
             raise OracleError(ERR_ARG)
         st = ctypes.c_int(0)
-        self._h = _L().og_new(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
-                              ctypes.byref(st))
+        if threads is None:
+            self._h = _L().og_new(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
+                                  ctypes.byref(st))
+        else:
+            self._h = _L().og_new_par(int(n), int(src.size), src.ctypes.data, dst.ctypes.data,
+                                      ctypes.byref(st), int(threads))
         if st.value != OK:
             raise OracleError(st.value)
         self.n = int(n)
@@ -129,6 +145,30 @@ class Graph:
         t = np.empty(self.n, np.uint64)
         total = int(_L().og_count(self._h, t.ctypes.data))
         return total, t
+
+    def count_par(self, threads: int = 0) -> int:
+        """T by the parallel CF edge iterator (0 threads = all host cores)."""
+        T = int(_L().og_count_par(self._h, None, int(threads)))
+        if T == (1 << 64) - 1:
+            raise OracleError(ERR_NOMEM)
+        return T
+
+    def count_per_vertex_par(self, threads: int = 0):
+        t = np.empty(self.n, np.uint64)
+        total = int(_L().og_count_par(self._h, t.ctypes.data, int(threads)))
+        if total == (1 << 64) - 1:
+            raise OracleError(ERR_NOMEM)
+        return total, t
+
+    def list_canonical_par(self, order: int = ORDER_DESC, threads: int = 0) -> np.ndarray:
+        total = int(_L().og_list_canonical_par(self._h, order, None, 0, int(threads)))
+        if total == (1 << 64) - 1:
+            raise OracleError(ERR_NOMEM)
+        out = np.empty((max(total, 1), 3), np.int32)
+        got = int(_L().og_list_canonical_par(self._h, order, out.ctypes.data, total, int(threads)))
+        if got != total:
+            raise OracleError(ERR_NOMEM)
+        return out[:total]
 
     def vertex_count(self, v: int) -> int:
         return int(_L().og_vertex_count(self._h, int(v)))
@@ -182,6 +222,11 @@ class Graph:
         out = np.empty((max(total, 1), 3), np.int32)
         _L().og_list_canonical(self._h, order, out.ctypes.data, total)
         return out[:total]
+
+
+def host_threads(threads: int = 0) -> int:
+    """Threads the parallel paths use (0 = all host cores)."""
+    return int(_L().og_threads(int(threads)))
 
 
 def stream_vertex_counts(n: int, src, dst, verts) -> np.ndarray:

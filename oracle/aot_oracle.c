@@ -39,10 +39,31 @@
  *                   in original ids.
  *  og_stream_vertex_counts  t(v) for a few sampled v straight from a raw edge
  *                   list, without building a graph (for huge inputs).
+ *
+ * Parallel paths (OpenMP; for the full-size parity tests and the CPU
+ * baseline).  The serial functions above stay the definition: a -m "not gpu"
+ * test checks each parallel function against them, and every count is still
+ * an exact uint64 (per-thread partial sums added at the end).
+ *
+ *  og_new_par       og_new with the per-vertex sort and dedup spread over
+ *                   threads (same cleaned graph).
+ *  og_count_par     T and t(v) by the edge iterator of Sec. 2.2 (Algorithm 1,
+ *                   CF) over the degree-ASCENDING orientation: for every
+ *                   oriented <u,v>, merge N+(u) with N+(v); each common w
+ *                   closes {u,v,w} once.  Parallel over u.
+ *  og_list_canonical_par  the canonical list of og_list_canonical, produced
+ *                   directly in its order: for x in eta order, for y in N+(x)
+ *                   ascending, the z of N+(y) (ascending) that are marked as
+ *                   members of N+(x).  Two passes (count per x, then write at
+ *                   the prefix offset), parallel over x.
+ *  og_threads       the number of threads the parallel paths use.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OG_OK 0
 #define OG_ERR_ARG 1
@@ -423,4 +444,234 @@ int og_stream_vertex_counts(int32_t n, int64_t num_edges, const int32_t* src,
   }
   free(mark);
   return OG_OK;
+}
+
+/* ---------------------------------------------------------- parallel paths */
+int og_threads(int threads) {
+#ifdef _OPENMP
+  return threads > 0 ? threads : omp_get_max_threads();
+#else
+  (void)threads;
+  return 1;
+#endif
+}
+
+og_graph* og_new_par(int32_t n, int64_t num_edges, const int32_t* src, const int32_t* dst,
+                     int* status, int threads) {
+  *status = OG_OK;
+  if (n < 0 || num_edges < 0) { *status = OG_ERR_ARG; return NULL; }
+  int bad = 0;
+  int nt = og_threads(threads);
+#pragma omp parallel for num_threads(nt) reduction(| : bad) schedule(static)
+  for (int64_t i = 0; i < num_edges; ++i)
+    bad |= (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n);
+  if (bad) { *status = OG_ERR_RANGE; return NULL; }
+  og_graph* g = (og_graph*)calloc(1, sizeof(og_graph));
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* off = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+  if (!g || !cnt || !off) { free(g); free(cnt); free(off); *status = OG_ERR_NOMEM; return NULL; }
+  g->n = n;
+  for (int64_t i = 0; i < num_edges; ++i) {
+    if (src[i] == dst[i]) continue;
+    cnt[src[i]]++;
+    cnt[dst[i]]++;
+  }
+  off[0] = 0;
+  for (int32_t v = 0; v < n; ++v) off[v + 1] = off[v] + cnt[v];
+  int32_t* adj = (int32_t*)malloc((size_t)(off[n] > 0 ? off[n] : 1) * sizeof(int32_t));
+  if (!adj) { free(g); free(cnt); free(off); *status = OG_ERR_NOMEM; return NULL; }
+  for (int32_t v = 0; v < n; ++v) cnt[v] = off[v];
+  for (int64_t i = 0; i < num_edges; ++i) {
+    int32_t a = src[i], b = dst[i];
+    if (a == b) continue;
+    adj[cnt[a]++] = b;
+    adj[cnt[b]++] = a;
+  }
+  /* sort each list and drop repeats inside its own range; cnt[v] = kept */
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1024)
+  for (int32_t v = 0; v < n; ++v) {
+    int64_t lo = off[v], hi = off[v + 1], w = lo;
+    qsort(adj + lo, (size_t)(hi - lo), sizeof(int32_t), cmp_i32);
+    for (int64_t k = lo; k < hi; ++k)
+      if (k == lo || adj[k] != adj[k - 1]) adj[w++] = adj[k];
+    cnt[v] = w - lo;
+  }
+  /* compact in place (left shifts only, in vertex order) */
+  int64_t w = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    int64_t lo = off[v];
+    if (w != lo) memmove(adj + w, adj + lo, (size_t)cnt[v] * sizeof(int32_t));
+    off[v] = w;
+    w += cnt[v];
+  }
+  off[n] = w;
+  free(cnt);
+  g->off = off;
+  g->adj = adj;
+  g->m = w / 2;
+  return g;
+}
+
+/* eta as in og_eta, through a thread-safe sort of (degree key, id) words */
+static int og_eta_keys(const og_graph* g, int order, int32_t* rank, int32_t* perm) {
+  int32_t n = g->n;
+  uint64_t* key = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+  if (!key) return OG_ERR_NOMEM;
+  for (int32_t v = 0; v < n; ++v) {
+    uint64_t d = (uint64_t)(g->off[v + 1] - g->off[v]);
+    uint64_t k = order == OG_ORDER_DESC ? (0xffffffffull - d) : d;
+    key[v] = (k << 32) | (uint32_t)v;
+  }
+  qsort(key, (size_t)n, sizeof(uint64_t), cmp_u64);
+  for (int32_t r = 0; r < n; ++r) {
+    perm[r] = (int32_t)(uint32_t)key[r];
+    rank[perm[r]] = r;
+  }
+  free(key);
+  return OG_OK;
+}
+
+/* Oriented out-CSR in rank space (same result as og_orient_alloc). */
+static int og_orient_par(const og_graph* g, int order, int nt, int32_t** rank_o, int32_t** perm_o,
+                         int64_t** off_o, int32_t** adj_o) {
+  int32_t n = g->n;
+  int32_t* rank = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  int32_t* perm = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  int64_t* off = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+  int32_t* adj = (int32_t*)malloc(((size_t)g->m + 1) * sizeof(int32_t));
+  if (!rank || !perm || !off || !adj || og_eta_keys(g, order, rank, perm) != OG_OK) {
+    free(rank); free(perm); free(off); free(adj);
+    return OG_ERR_NOMEM;
+  }
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1024)
+  for (int32_t r = 0; r < n; ++r) {
+    int32_t v = perm[r];
+    int64_t c = 0;
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i) c += rank[g->adj[i]] > r;
+    off[r + 1] = c;
+  }
+  off[0] = 0;
+  for (int32_t r = 0; r < n; ++r) off[r + 1] += off[r];
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1024)
+  for (int32_t r = 0; r < n; ++r) {
+    int32_t v = perm[r];
+    int64_t k = off[r];
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      int32_t rr = rank[g->adj[i]];
+      if (rr > r) adj[k++] = rr;
+    }
+    qsort(adj + off[r], (size_t)(k - off[r]), sizeof(int32_t), cmp_i32);
+  }
+  *rank_o = rank; *perm_o = perm; *off_o = off; *adj_o = adj;
+  return OG_OK;
+}
+
+/* T, and t(v) (original ids) when t != NULL.  Returns (uint64_t)-1 when out
+ * of memory. */
+uint64_t og_count_par(const og_graph* g, uint64_t* t, int threads) {
+  int nt = og_threads(threads);
+  int32_t *rank, *perm, *adj;
+  int64_t* off;
+  if (og_orient_par(g, OG_ORDER_ASC, nt, &rank, &perm, &off, &adj) != OG_OK) return (uint64_t)-1;
+  int32_t n = g->n;
+  uint64_t* tl = NULL; /* one rank-space count array per thread */
+  if (t) {
+    tl = (uint64_t*)calloc((size_t)nt * ((size_t)n + 1), sizeof(uint64_t));
+    if (!tl) { free(rank); free(perm); free(off); free(adj); return (uint64_t)-1; }
+  }
+  uint64_t total = 0;
+#pragma omp parallel num_threads(nt) reduction(+ : total)
+  {
+#ifdef _OPENMP
+    uint64_t* my = tl ? tl + (size_t)omp_get_thread_num() * ((size_t)n + 1) : NULL;
+#else
+    uint64_t* my = tl;
+#endif
+#pragma omp for schedule(dynamic, 64)
+    for (int32_t u = 0; u < n; ++u) {
+      for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+        int32_t v = adj[i];
+        /* every entry of N+(v) is above v, so the merge starts after v in N+(u) */
+        int64_t p = i + 1, pe = off[u + 1], q = off[v], qe = off[v + 1];
+        uint64_t c = 0;
+        while (p < pe && q < qe) {
+          int32_t x = adj[p], y = adj[q];
+          if (x < y) { ++p; continue; }
+          if (y < x) { ++q; continue; }
+          ++c;
+          if (my) my[x]++;
+          ++p; ++q;
+        }
+        total += c;
+        if (my) { my[u] += c; my[v] += c; }
+      }
+    }
+  }
+  if (t) {
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int32_t r = 0; r < n; ++r) {
+      uint64_t s = 0;
+      for (int k = 0; k < nt; ++k) s += tl[(size_t)k * ((size_t)n + 1) + r];
+      t[perm[r]] = s;
+    }
+    free(tl);
+  }
+  free(rank); free(perm); free(off); free(adj);
+  return total;
+}
+
+/* Canonical list (see og_list_canonical).  Returns T; writes only if
+ * out != NULL and cap >= T; (uint64_t)-1 when out of memory. */
+uint64_t og_list_canonical_par(const og_graph* g, int order, int32_t* out, uint64_t cap,
+                               int threads) {
+  int nt = og_threads(threads);
+  int32_t *rank, *perm, *adj;
+  int64_t* off;
+  if (og_orient_par(g, order, nt, &rank, &perm, &off, &adj) != OG_OK) return (uint64_t)-1;
+  int32_t n = g->n;
+  uint64_t* per = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+  uint8_t* marks = (uint8_t*)calloc((size_t)nt * ((size_t)n + 1), 1);
+  if (!per || !marks) {
+    free(per); free(marks); free(rank); free(perm); free(off); free(adj);
+    return (uint64_t)-1;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      uint64_t run = 0;
+      for (int32_t x = 0; x < n; ++x) { uint64_t c = per[x]; per[x] = run; run += c; }
+      per[n] = run;
+      if (!out || cap < run) break;
+    }
+#pragma omp parallel num_threads(nt)
+    {
+#ifdef _OPENMP
+      uint8_t* mk = marks + (size_t)omp_get_thread_num() * ((size_t)n + 1);
+#else
+      uint8_t* mk = marks;
+#endif
+#pragma omp for schedule(dynamic, 64)
+      for (int32_t x = 0; x < n; ++x) {
+        for (int64_t i = off[x]; i < off[x + 1]; ++i) mk[adj[i]] = 1;
+        uint64_t k = pass == 1 ? per[x] : 0;
+        for (int64_t i = off[x]; i < off[x + 1]; ++i) {
+          int32_t y = adj[i];
+          for (int64_t j = off[y]; j < off[y + 1]; ++j) {
+            int32_t z = adj[j];
+            if (!mk[z]) continue;
+            if (pass == 1) {
+              out[3 * k] = perm[x];
+              out[3 * k + 1] = perm[y];
+              out[3 * k + 2] = perm[z];
+            }
+            ++k;
+          }
+        }
+        if (pass == 0) per[x] = k;
+        for (int64_t i = off[x]; i < off[x + 1]; ++i) mk[adj[i]] = 0;
+      }
+    }
+  }
+  uint64_t total = per[n];
+  free(per); free(marks); free(rank); free(perm); free(off); free(adj);
+  return total;
 }

@@ -2,11 +2,40 @@
 // destroy.  The heavy entry points live next to their kernels.
 #include "aot_internal.cuh"
 
+#include <map>
 #include <mutex>
+#include <utility>
 
 using namespace aot;
 
 namespace aot {
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void*>, size_t> g_attr_set;  // (device, kernel) -> bytes
+static std::map<int, int> g_sms;                                    // device -> SM count
+
+aot_status ensure_dyn_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return AOT_OK;  // the default limit
+  int dev = 0;
+  AOT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t& cur = g_attr_set[std::make_pair(dev, func)];
+  if (cur >= bytes) return AOT_OK;
+  AOT_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return AOT_OK;
+}
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  int& sms = g_sms[dev];
+  if (sms <= 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
 static std::mutex g_default_mu;
 static Tuning g_default_tuning;
 static const void* g_default_router = nullptr;

@@ -18,6 +18,8 @@
 // find their item by a 5-step shuffle search over the exclusive prefix of
 // walk lengths, probe H, and count with __ballot_sync/__popc.
 // Work is handed out by per-bin atomic queues (persistent grids).
+#include <vector>
+
 #include "aot_internal.cuh"
 #include "aot_kparams.cuh"
 
@@ -843,32 +845,17 @@ static const char* mode_name(const char* base) {
   return kHubNames[MODE];
 }
 
-static int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
-}
-
 template <int MODE>
 static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
   const uint32_t nw = g->bin_count[BIN_WARP], nc = g->bin_count[BIN_CTA], nh = g->bin_count[BIN_HUB];
   const int sms = sm_count();
   // a warp per pivot with ts_max-slot tables; warps per CTA chosen (8, 4, 2
   // or 1) for the most resident warps
-  static size_t warp_attr[5] = {0, 0, 0, 0, 0};
   auto launch_warps = [&](uint32_t count, uint32_t ts_max, int q, const char* name) -> aot_status {
     const size_t per_warp = (size_t)(MODE == M_VERTEX ? 2 : 1) * ts_max * sizeof(uint32_t);
     const size_t smem_cap = 227 * 1024;
     const size_t attr = per_warp * 8 < smem_cap ? per_warp * 8 : smem_cap;
-    if (attr > 48 * 1024 && warp_attr[MODE] < attr) {
-      AOT_CUDA(cudaFuncSetAttribute(k_warp_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)attr));
-      warp_attr[MODE] = attr;
-    }
+    AOT_TRY(ensure_dyn_smem((const void*)k_warp_pivots<MODE>, attr));
     int warps_per_block = 1, per_sm = 0, best = -1;
     for (int w = 8; w >= 1; w >>= 1) {
       const size_t sm_bytes = (size_t)w * per_warp;
@@ -905,11 +892,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     P.num_pivots = nc;
     const uint32_t ts_max = cta_ts;
     size_t smem = (size_t)ts_max * 2 * sizeof(uint32_t);
-    static size_t attr_done[5] = {0, 0, 0, 0, 0};
-    if (attr_done[MODE] < smem) {
-      AOT_CUDA(cudaFuncSetAttribute(k_cta_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr_done[MODE] = smem;
-    }
+    AOT_TRY(ensure_dyn_smem((const void*)k_cta_pivots<MODE>, smem));
     const int threads = g->tune.cta_threads;
     int per_sm = 0;
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cta_pivots<MODE>, threads, smem));
@@ -951,12 +934,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
       AOT_TRY(last_launch());
     }
     const size_t seg_smem = seg_smem_bytes(seg_bits);
-    static bool seg_attr[5] = {false, false, false, false, false};
-    if (!seg_attr[MODE]) {
-      AOT_CUDA(cudaFuncSetAttribute(k_seg_pivots<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)seg_smem_bytes(SEG_BITS_MAX)));
-      seg_attr[MODE] = true;
-    }
+    AOT_TRY(ensure_dyn_smem((const void*)k_seg_pivots<MODE>, seg_smem_bytes(SEG_BITS_MAX)));
     P.pivots = dp;
     P.num_pivots = nh;
     int per_sm = 0;
@@ -971,7 +949,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_KERNEL("k_hub_info", s)
       k_hub_info<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->hubinfo);
     AOT_TRY(last_launch());
-    uint32_t* hp = new uint32_t[4 * (size_t)nh];
+    std::vector<uint32_t> hpv(4 * (size_t)nh);
+    uint32_t* hp = hpv.data();
     AOT_CUDA(cudaMemcpyAsync(hp, g->hubinfo, sizeof(uint32_t) * 4 * nh, cudaMemcpyDeviceToHost, s));
     AOT_CUDA(cudaStreamSynchronize(s));
     const uint32_t words = (uint32_t)(((int64_t)g->n + 31) / 32);
@@ -1011,7 +990,6 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
         k_hub_bits<<<sgrid, 256, 0, s>>>(G, g->off, g->adj, false);
       AOT_TRY(last_launch());
     }
-    delete[] hp;
   }
   return AOT_OK;
 }

@@ -34,6 +34,14 @@ inline aot_status last_launch() {
   return cudaGetLastError() == cudaSuccess ? AOT_OK : AOT_ERR_CUDA;
 }
 
+// Raise the dynamic shared-memory limit of kernel `func` on the CURRENT device
+// to at least `bytes`.  cudaFuncSetAttribute acts on one device only, so the
+// largest value set so far is remembered per (device, kernel), under a mutex
+// (calls may come from several host threads and devices).
+aot_status ensure_dyn_smem(const void* func, size_t bytes);
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
+
 // Launch accounting: AOT_KERNEL(name, stream) <launch statement>;
 // counts the launch and, while profiling is on, brackets it with events.
 struct ProfScope {

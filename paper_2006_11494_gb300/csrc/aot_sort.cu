@@ -263,12 +263,7 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
   uint32_t* offs = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + hist_bytes);
   void* stmp = static_cast<char*>(tmp) + 2 * hist_bytes;
   size_t smem = sizeof(K) * RS_TILE + (VALS ? sizeof(uint32_t) * RS_TILE : 0);
-  static bool attr_set = false;  // per template instance
-  if (!attr_set) {
-    AOT_CUDA(cudaFuncSetAttribute(k_radix_scatter<K, VALS>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
+  AOT_TRY(ensure_dyn_smem((const void*)k_radix_scatter<K, VALS>, smem));
   K* a = keys;
   K* b = keys_alt;
   uint32_t* va = vals;

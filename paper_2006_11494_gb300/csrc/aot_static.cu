@@ -14,10 +14,15 @@
 //    call on each device (with that device current) asks the runtime for the
 //    array's device address with cudaGetSymbolAddress and caches it; make that
 //    first call outside any stream capture.
+//  - The cached address belongs to the device's current context: after
+//    cudaDeviceReset it is stale, so a process that resets a device must not
+//    call this entry point on that device again.
 //  - All calls share the one array and it keeps the previous call's contents;
 //    the orientation clears every part that must start at zero.  Two calls
 //    whose work overlaps on the GPU (different streams or host threads) race
-//    on the array: serialise them.
+//    on the array: serialise them.  A call that fails after it has queued
+//    kernels waits for them before it returns, so a retry on another stream
+//    never overlaps them.
 #include <mutex>
 
 #include "aot_internal.cuh"
@@ -54,12 +59,15 @@ extern "C" aot_status aot_count_per_vertex_static(const int32_t* d_src, const in
   aot_graph* g = nullptr;
   st = aot_orient(d_src, d_dst, num_edges, num_vertices, AOT_FLAG_NO_LIST, scratch,
                   (size_t)AOT_STATIC_SCRATCH_BYTES, stream, &g);
-  if (st != AOT_OK) return st;
-  if (d_counts) {
-    st = aot_count_per_vertex(g, AOT_ROUTE_PLAIN, d_counts, h_total, stream);
-  } else {
-    st = aot_count(g, AOT_ROUTE_PLAIN, h_total, stream);
+  if (st == AOT_OK) {
+    if (d_counts) {
+      st = aot_count_per_vertex(g, AOT_ROUTE_PLAIN, d_counts, h_total, stream);
+    } else {
+      st = aot_count(g, AOT_ROUTE_PLAIN, h_total, stream);
+    }
+    aot_graph_destroy(g);
   }
-  aot_graph_destroy(g);
+  // kernels queued before a failure still use the shared array: let them finish
+  if (st != AOT_OK) cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
   return st;
 }
