@@ -317,3 +317,25 @@ def test_side_stream():
         import paper_2006_11494_gb300 as aot
         g = aot.OrientedGraph(src, dst, n, 0, st)
         assert g.count(stream=st) == T_ref
+
+
+def test_second_device_after_the_first():
+    """Kernels that need more than 48 KB of dynamic shared memory get their
+    limit raised on every device they run on: orient and count on cuda:1
+    after cuda:0 (skipped on a one-GPU machine)."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    import paper_2006_11494_gb300 as aot
+    n, s, d = gg.rmat_cfg(14, 3)
+    ref = oracle.Graph(n, s, d)
+    T_ref, t_ref = ref.count_per_vertex()
+    for dev in ("cuda:0", "cuda:1"):
+        with torch.cuda.device(dev):
+            src = torch.from_numpy(s).to(dev)
+            dst = torch.from_numpy(d).to(dev)
+            g = aot.OrientedGraph(src, dst, n)
+            assert g.count() == T_ref
+            T, t = g.count_per_vertex()
+            assert T == T_ref and np.array_equal(u64(t), t_ref)
+            g.close()
