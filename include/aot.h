@@ -154,8 +154,13 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * entries remain, else of 128), shorter ones by a thread each; hub_mode 1:
  * global bitmaps of n bits, hub_bitmaps (1..32) hubs at a time, all CTAs
  * sharing their items.  cta_threads is a multiple of 32 in [32, 1024].
+ * tile_bits (hub_mode 0): 0, or in [16, 31]: the hub tasks are handed out
+ * tile by tile of the walked out-lists, a tile being the lists that fill
+ * 2^tile_bits consecutive adjacency entries, so that the lists walked at the
+ * same time stay in L2; 0 hands them out pivot by pivot.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
- * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512.
+ * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
+ * tile_bits 23.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
@@ -166,6 +171,7 @@ typedef struct {
   uint32_t seg_bits;
   uint32_t seg_long;
   uint32_t seg_wide;
+  uint32_t tile_bits;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */
@@ -307,7 +313,7 @@ aot_status aot_get_default_tuning(aot_tuning* t);
 
 /* Autotuner: coordinate search over the bin thresholds (CTA-hash cutoff,
  * warp cutoff), CTA size, the segmented walk's short/long and 128/256-entry
- * thresholds and the bitmap segment width, timing each candidate on this
+ * thresholds, the bitmap segment width and the walked-list tile size, timing each candidate on this
  * graph with CUDA events (best of reps) in mode 0 (count) or 1 (per-vertex
  * count); a candidate replaces the current tuning only when it is at least
  * 1 % faster.  The chosen tuning is set on the graph and returned in

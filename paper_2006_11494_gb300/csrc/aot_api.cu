@@ -52,7 +52,8 @@ static bool tuning_valid(const aot_tuning* t) {
            t->cta_max_outdeg < t->warp_max_outdeg || t->cta_threads < 32 || t->cta_threads > 1024 ||
            (t->cta_threads & 31) || t->hub_bitmaps < 1 || t->hub_bitmaps > Tuning().hub_bitmaps ||
            t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
-           (t->seg_bits & 31) || t->seg_long > (1u << 30) || t->seg_wide > (1u << 30));
+           (t->seg_bits & 31) || t->seg_long > (1u << 30) || t->seg_wide > (1u << 30) ||
+           (t->tile_bits != 0 && (t->tile_bits < 16 || t->tile_bits > 31)));
 }
 }  // namespace aot
 
@@ -67,6 +68,7 @@ extern "C" aot_status aot_set_default_tuning(const aot_tuning* t) {
   g_default_tuning.seg_bits = t->seg_bits;
   g_default_tuning.seg_long = t->seg_long;
   g_default_tuning.seg_wide = t->seg_wide;
+  g_default_tuning.tile_bits = t->tile_bits;
   return AOT_OK;
 }
 
@@ -88,6 +90,7 @@ extern "C" aot_status aot_get_default_tuning(aot_tuning* t) {
   t->seg_bits = d.seg_bits;
   t->seg_long = d.seg_long;
   t->seg_wide = d.seg_wide;
+  t->tile_bits = d.tile_bits;
   return AOT_OK;
 }
 
@@ -159,6 +162,7 @@ extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
   t->seg_bits = g->tune.seg_bits;
   t->seg_long = g->tune.seg_long;
   t->seg_wide = g->tune.seg_wide;
+  t->tile_bits = g->tune.tile_bits;
   return AOT_OK;
 }
 
@@ -173,6 +177,7 @@ extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, ao
   g->tune.seg_bits = t->seg_bits;
   g->tune.seg_long = t->seg_long;
   g->tune.seg_wide = t->seg_wide;
+  g->tune.tile_bits = t->tile_bits;
   aot_status st = bin_pivots(g, reinterpret_cast<cudaStream_t>(stream));
   if (st != AOT_OK) g->tune = old;
   return st;

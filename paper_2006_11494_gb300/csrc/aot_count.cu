@@ -395,20 +395,81 @@ __device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict_
   return lo + (uint32_t)__popc(__ballot_sync(FULL, less));
 }
 
+// first index in [lo, hi) where less(idx) is false (less holds on a prefix);
+// all 32 lanes call it
+template <class Less>
+__device__ __forceinline__ uint32_t warp_partition(uint32_t lo, uint32_t hi, Less less) {
+  const unsigned lane = lane_id();
+  while (hi - lo > 32) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t idx = lo + lane * step;
+    const bool l = idx < hi && less(idx);
+    const int c = __popc(__ballot_sync(FULL, l));
+    if (c == 0) return lo;
+    const uint32_t nlo = lo + (uint32_t)(c - 1) * step + 1;
+    const uint32_t nhi = min(hi, lo + (uint32_t)c * step);
+    lo = nlo;
+    hi = nhi;
+  }
+  const uint32_t idx = lo + lane;
+  const bool l = idx < hi && less(idx);
+  return lo + (uint32_t)__popc(__ballot_sync(FULL, l));
+}
+
 constexpr uint32_t SEG_MAXB = 512;  // segment bounds of one pivot held in shared memory
 
-// Per hub pivot: its tasks, and its segments + 1 (the bounds of N+(p) that
-// split its rank range [min N+(p), max N+(p)] into segments of seg_bits).
-__global__ void k_seg_task_counts(const uint32_t* __restrict__ pivots, uint32_t nh,
-                                  const uint32_t* __restrict__ wofs, const uint32_t* __restrict__ off,
-                                  const uint32_t* __restrict__ adj, uint32_t seg_bits,
-                                  uint32_t* __restrict__ cnt, uint32_t* __restrict__ nbound) {
-  uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= nh) return;
-  uint32_t p = pivots[h];
-  cnt[h] = (wofs[p + 1] - wofs[p] + SEG_ITEMS - 1) / SEG_ITEMS;
-  const uint32_t lo = adj[off[p]], hi = adj[off[p + 1] - 1] + 1;  // hubs have deg+ > 0
-  nbound[h] = (hi - lo + seg_bits - 1) / seg_bits + 1;
+// Work groups of the hub pivots, a warp per pivot.  A pivot's positive items
+// come first, sorted by their walked vertex v (larger rank than the pivot),
+// then its negative items (walked vertex of smaller rank).  With G >= 2
+// groups, groups 0 .. G-2 hold the positive items by the tile of v's
+// out-list, tile(v) = off[v] >> tile_bits (the out-lists of one tile fill
+// 2^tile_bits consecutive adjacency entries; the last tile group also takes
+// every later tile), and group G-1 the negative items; G = 1 is one group of
+// all items.  Group g of hub h spans items [bound(g), bound(g+1)) with
+// bound(0) = wofs[p], bound(G) = wofs[p+1] and the inner bounds in
+// ist[(g-1) nh + h]; it takes ceil(size / SEG_ITEMS) tasks (tcnt[g nh + h]).
+// Groups are laid out tile-major, so the task queue hands out every pivot's
+// items of tile 0 first, then tile 1, ...: blocks that run at the same time
+// walk the same out-lists, which stay in L2.
+// Also: nbound[h] = segments + 1 of the pivot's rank range [min N+(p),
+// max N+(p)] in segments of seg_bits.
+__device__ __forceinline__ uint32_t group_bound(const uint32_t* ist, const uint32_t* wofs, uint32_t p,
+                                                uint32_t h, uint32_t nh, uint32_t G, uint32_t g) {
+  return g == 0 ? wofs[p] : (g == G ? wofs[p + 1] : ist[(size_t)(g - 1) * nh + h]);
+}
+
+__global__ void k_seg_groups(const uint32_t* __restrict__ pivots, uint32_t nh,
+                             const uint32_t* __restrict__ wofs, const uint32_t* __restrict__ wvert,
+                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                             uint32_t G, int tile_bits, uint32_t seg_bits,
+                             uint32_t* __restrict__ ist, uint32_t* __restrict__ tcnt,
+                             uint32_t* __restrict__ nbound) {
+  const unsigned lane = lane_id();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
+    const uint32_t p = pivots[h];
+    const uint32_t b = wofs[p], e = wofs[p + 1];
+    if (G >= 2) {
+      const uint32_t pe = warp_partition(b, e, [&](uint32_t i) { return wvert[i] > p; });
+      for (uint32_t g = 1; g + 1 < G; ++g) {
+        const uint32_t x = warp_partition(b, pe, [&](uint32_t i) {
+          return (off[wvert[i]] >> tile_bits) < g;
+        });
+        if (lane == 0) ist[(size_t)(g - 1) * nh + h] = x;
+      }
+      if (lane == 0) ist[(size_t)(G - 2) * nh + h] = pe;
+    }
+    __syncwarp();
+    for (uint32_t g = lane; g < G; g += 32) {
+      const uint32_t a = group_bound(ist, wofs, p, h, nh, G, g);
+      const uint32_t z = group_bound(ist, wofs, p, h, nh, G, g + 1);
+      tcnt[(size_t)g * nh + h] = (z - a + SEG_ITEMS - 1) / SEG_ITEMS;
+    }
+    if (lane == 0) {
+      const uint32_t lo = adj[off[p]], hi = adj[off[p + 1] - 1] + 1;  // hubs have deg+ > 0
+      nbound[h] = (hi - lo + seg_bits - 1) / seg_bits + 1;
+    }
+  }
 }
 
 // Segment bounds of every hub pivot, a warp per pivot: bound s is the first
@@ -623,9 +684,13 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
   if (x >= y) nv = NONE;
 }
 
+// Tasks: task_ofs[k] (k = g nh + h, K = G nh of them, plus the total) is the
+// first task of work group g of hub h, whose items are [bound(g), bound(g+1))
+// (k_seg_groups).
 template <int MODE>
 __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const uint32_t* __restrict__ task_ofs,
-                                                               uint32_t nh, uint32_t seg_bits,
+                                                               const uint32_t* __restrict__ ist,
+                                                               uint32_t nh, uint32_t G, uint32_t seg_bits,
                                                                uint32_t seg_long, uint32_t seg_wide,
                                                                const uint32_t* __restrict__ bofs,
                                                                const uint32_t* __restrict__ bnd,
@@ -639,11 +704,12 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
   uint32_t* ih = nextv + SEG_ITEMS;
   uint32_t* longs = ih + SEG_ITEMS;                              // long items of the task
   uint8_t* islong = reinterpret_cast<uint8_t*>(longs + SEG_ITEMS);
-  __shared__ uint32_t s_task, s_hub, s_pe, s_next, s_nlong;
+  __shared__ uint32_t s_task, s_grp, s_pe, s_next, s_nlong;
   __shared__ uint32_t s_bound[SEG_MAXB];  // this pivot's segment bounds (when they fit)
   __shared__ unsigned long long s_hits, s_stage;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-  const uint32_t ntasks = task_ofs[nh];
+  const uint32_t K = G * nh;
+  const uint32_t ntasks = task_ofs[K];
   const bool have_bounds = bnd != nullptr && (uint64_t)bofs[nh] <= bcap;
   for (uint32_t i = threadIdx.x; i <= seg_words; i += blockDim.x) bm[i] = 0;  // + guard word
   uint64_t found = 0;
@@ -657,8 +723,8 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     __syncthreads();
     const uint32_t task = s_task;
     if (task >= ntasks) break;
-    if (wid == 0) {  // largest h with task_ofs[h] <= task (32-ary search)
-      uint32_t lo = 0, hi = nh;
+    if (wid == 0) {  // largest k with task_ofs[k] <= task (32-ary search)
+      uint32_t lo = 0, hi = K;
       while (hi - lo > 1) {
         const uint32_t step = (hi - lo + 31) / 32;
         const uint32_t idx = lo + lane * step;
@@ -669,10 +735,11 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         lo = nlo;
         hi = nhi;
       }
-      if (lane == 0) s_hub = lo;
+      if (lane == 0) s_grp = lo;
     }
     __syncthreads();
-    const uint32_t h = s_hub;
+    const uint32_t kg = s_grp;
+    const uint32_t h = kg % nh, grp = kg / nh;
     const uint32_t p = P.pivots[h];
     if (P.rprobe && P.rprobe[p] == 0) {  // every item of p takes another route
       __syncthreads();
@@ -684,8 +751,8 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     const bool use_bounds = nb != 0 && nb <= SEG_MAXB;
     if (use_bounds)
       for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_bound[t] = bnd[bofs[h] + t];
-    const uint32_t i0 = P.wofs[p] + (task - task_ofs[h]) * SEG_ITEMS;
-    const uint32_t i1 = min(i0 + SEG_ITEMS, P.wofs[p + 1]);
+    const uint32_t i0 = group_bound(ist, P.wofs, p, h, nh, G, grp) + (task - task_ofs[kg]) * SEG_ITEMS;
+    const uint32_t i1 = min(i0 + SEG_ITEMS, group_bound(ist, P.wofs, p, h, nh, G, grp + 1));
     const uint32_t nk = i1 - i0;
     int live = 0;  // does any item of this task walk anything?
     for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
@@ -903,28 +970,40 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_TRY(last_launch());
   }
   if (nh && g->tune.hub_mode == 0) {
-    // segmented shared-memory bitmap: tasks = (pivot, block of SEG_ITEMS items)
+    // segmented shared-memory bitmap: tasks = (work group of a pivot, block
+    // of SEG_ITEMS items), groups = tiles of the walked out-lists + negatives
     const uint32_t* dp = g->bin_pivots + nw + nc;
-    // hubinfo (4n words): task counts | task offsets | bound counts | bound
-    // offsets | bounds (what is left: the bounds are skipped when they do not fit)
     const uint32_t seg_bits = g->tune.seg_bits;
-    const size_t n4 = 4 * (size_t)g->n;
-    uint32_t* cnt = g->hubinfo;
-    uint32_t* task_ofs = g->hubinfo + g->n;
-    uint32_t* nbound = g->hubinfo + 2 * (size_t)g->n;
+    // hubinfo (4n words): inner group bounds ((G-1) nh) | task counts, then
+    // offsets (G nh + 1) | bound counts (nh) | bound offsets (nh + 1) | segment
+    // bounds (what is left: they are skipped when they do not fit).  G groups
+    // need (2G + 1) nh + 2 <= 4n words; G = 1 always fits (nh <= n).
+    const uint64_t n4 = 4 * (uint64_t)g->n;
+    const int tb = (int)g->tune.tile_bits;
+    const uint64_t gmax = ((n4 - 2) / nh - 1) / 2;
+    uint64_t gw = tb ? (((uint64_t)g->m - 1) >> tb) + 2 : 1;  // tiles + the negative items
+    if (gw > gmax) gw = gmax;
+    if (gw < 2) gw = 1;
+    const uint32_t G = (uint32_t)gw;
+    const uint32_t K = G * nh;
+    uint32_t* ist = g->hubinfo;
+    uint32_t* task_ofs = ist + (size_t)(G - 1) * nh;
+    uint32_t* nbound = task_ofs + K + 1;
     uint32_t* bofs = nbound + nh;
     uint32_t* bnd = bofs + nh + 1;
-    const size_t used = (size_t)(bnd - g->hubinfo);
+    const uint64_t used = (uint64_t)(bnd - g->hubinfo);
     // every pivot has at most ceil(n / seg_bits) segments: take the bounds only
     // when that many fit (this also keeps the 32-bit offsets exact)
     const uint64_t worst = (uint64_t)nh * (((uint64_t)g->n + seg_bits - 1) / seg_bits + 1);
-    const uint64_t room = used < n4 ? (uint64_t)(n4 - used) : 0;
+    const uint64_t room = used < n4 ? n4 - used : 0;
     const uint64_t bcap = worst <= room && worst < 0xffffffffull ? room : 0;
-    AOT_KERNEL("k_seg_task_counts", s)
-      k_seg_task_counts<<<(nh + 255) / 256, 256, 0, s>>>(dp, nh, g->wofs, g->off, g->adj, seg_bits, cnt,
-                                                         nbound);
+    int64_t ggrid = ((int64_t)nh * 32 + 255) / 256;
+    if (ggrid > (int64_t)sms * 8) ggrid = (int64_t)sms * 8;
+    AOT_KERNEL("k_seg_groups", s)
+      k_seg_groups<<<(unsigned)ggrid, 256, 0, s>>>(dp, nh, g->wofs, g->wvert, g->off, g->adj, G, tb,
+                                                   seg_bits, ist, task_ofs, nbound);
     AOT_TRY(last_launch());
-    AOT_TRY(scan_u32_u32(cnt, task_ofs, nh, g->scan_tmp, s));
+    AOT_TRY(scan_u32_u32(task_ofs, task_ofs, K, g->scan_tmp, s));
     if (bcap) {
       AOT_TRY(scan_u32_u32(nbound, bofs, nh, g->scan_tmp, s));
       int64_t bgrid = ((int64_t)nh * 32 + 255) / 256;
@@ -941,7 +1020,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
-          P, task_ofs, nh, seg_bits, g->tune.seg_long, g->tune.seg_wide, bofs, bcap ? bnd : nullptr, bcap);
+          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, bofs, bcap ? bnd : nullptr,
+          bcap);
     AOT_TRY(last_launch());
   } else if (nh) {
     // hub descriptors on the host (hubs are few): pivot, first item, end item, deg+
@@ -1234,6 +1314,12 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
     for (uint32_t sb : segs) {
       aot_tuning t = cur;
       t.seg_bits = sb;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t tiles[] = {0u, 21u, 22u, 23u, 24u, 25u};
+    for (uint32_t tb : tiles) {
+      aot_tuning t = cur;
+      t.tile_bits = tb;
       AOT_TRY(trial(t));
     }
     AOT_TRY(aot_graph_set_tuning(g, &cur, stream));

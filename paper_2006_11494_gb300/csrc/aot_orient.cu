@@ -136,34 +136,54 @@ __device__ __forceinline__ void edge_item(int64_t e, const uint32_t* __restrict_
   }
 }
 
+// items per pivot, and posflag[e] = 1 for a positive edge (its pivot is its tail)
 __global__ void k_item_count(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
                              const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
-                             int64_t m, uint32_t* __restrict__ items) {
+                             int64_t m, uint32_t* __restrict__ items, uint32_t* __restrict__ posflag) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = e < m;
   uint32_t p = 0, x;
   uint2 r;
-  if (act) edge_item(e, esrc, adj, off, outdeg, p, x, r);
+  if (act) {
+    edge_item(e, esrc, adj, off, outdeg, p, x, r);
+    posflag[e] = p == esrc[e] ? 1u : 0u;
+  }
   agg_inc(items, p, act);
 }
 
+// Item slots.  A pivot's positive items come first, in out-list order (so
+// sorted by the walked vertex): the slot of positive edge e of row u is its
+// rank among the row's positive edges, from the exclusive scan pscan of the
+// positive flags.  Negative items follow in arrival order (atomic cursor).
 __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
                             int64_t m, const uint32_t* __restrict__ wofs,
-                            uint32_t* __restrict__ cursor, uint2* __restrict__ witem,
-                            uint32_t* __restrict__ wvert, uint32_t* __restrict__ wedge) {
+                            const uint32_t* __restrict__ pscan, uint32_t* __restrict__ cursor,
+                            uint2* __restrict__ witem, uint32_t* __restrict__ wvert,
+                            uint32_t* __restrict__ wedge) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = e < m;
   uint32_t p = 0, x = 0;
   uint2 r = make_uint2(0, 0);
-  if (act) edge_item(e, esrc, adj, off, outdeg, p, x, r);
-  unsigned grp = __match_any_sync(FULL, act ? p : 0xffffffffu);
+  bool pos = false;
+  if (act) {
+    edge_item(e, esrc, adj, off, outdeg, p, x, r);
+    pos = p == esrc[e];
+  }
+  const bool neg = act && !pos;
+  unsigned grp = __match_any_sync(FULL, neg ? p : 0xffffffffu);
   unsigned leader = (unsigned)(__ffs(grp) - 1);
   uint32_t base = 0;
-  if (act && lane_id() == leader) base = atomicAdd(&cursor[p], (uint32_t)__popc(grp));
+  if (neg && lane_id() == leader) base = atomicAdd(&cursor[p], (uint32_t)__popc(grp));
   base = __shfl_sync(FULL, base, leader);
   if (act) {
-    uint32_t slot = wofs[p] + base + (uint32_t)__popc(grp & lanemask_lt());
+    uint32_t slot;
+    if (pos) {
+      slot = wofs[p] + (pscan[e] - pscan[off[p]]);
+    } else {
+      const uint32_t npos = pscan[off[p + 1]] - pscan[off[p]];
+      slot = wofs[p] + npos + base + (uint32_t)__popc(grp & lanemask_lt());
+    }
     witem[slot] = r;
     wvert[slot] = x;
     wedge[slot] = (uint32_t)e;
@@ -479,10 +499,14 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   g->witem = reinterpret_cast<uint2*>(L.keysA);
   g->wvert = reinterpret_cast<uint32_t*>(L.keysB);
   g->wedge = reinterpret_cast<uint32_t*>(L.keysB) + (E > 0 ? E : 1);
+  // positive flags, then (in place) their exclusive scan: L.pos holds E + 1 >= m + 1 words
+  uint32_t* pscan = L.pos;
   if (m > 0) {
     AOT_KERNEL("k_item_count", s)
-      k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items);
+      k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items, pscan);
     if (last_launch()) return fail(AOT_ERR_CUDA);
+    aot_status st = scan_u32_u32(pscan, pscan, m, L.tmp, s);
+    if (st) return fail(st);
   }
   if (n > 0) {
     aot_status st = scan_u32_u32(L.items, L.wofs, n, L.tmp, s);
@@ -493,8 +517,8 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   }
   if (m > 0) {
     AOT_KERNEL("k_item_fill", s)
-      k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, L.bin_flag,
-                                             g->witem, g->wvert, g->wedge);
+      k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, pscan,
+                                             L.bin_flag, g->witem, g->wvert, g->wedge);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {

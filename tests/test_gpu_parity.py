@@ -126,10 +126,23 @@ def test_chunglu_full_parity():
     # every pivot on the bitmap path with 1024-rank segments: the per-pivot
     # segment bounds do not fit their scratch, so each segment end is searched
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024),
+    # walked-list tiles: none, several (clamped when most pivots are hubs)
+    dict(tile_bits=0),
+    dict(warp_max_outdeg=64, cta_max_outdeg=64, tile_bits=16),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, tile_bits=16),
 ])
 def test_every_bin_gives_the_same_answer(tuning):
     n, s, d = gg.rmat_cfg(13, 7)
     check_full(n, s, d, tuning=tuning)
+
+
+@pytest.mark.parametrize("tile_bits,seg_bits", [(16, 1572864), (17, 4096), (0, 4096)])
+def test_walk_tiles(tile_bits, seg_bits):
+    """Hub tasks handed out tile by tile of the walked out-lists (16 tiles of
+    2^16 entries at R-MAT scale 16), with one or many bitmap segments."""
+    n, s, d = gg.rmat_cfg(16, 5)
+    check_full(n, s, d, tuning=dict(warp_max_outdeg=32, cta_max_outdeg=128, tile_bits=tile_bits,
+                                    seg_bits=seg_bits))
 
 
 @pytest.mark.parametrize("case", ["rmat12", "er", "wheel", "k40", "chunglu"])
