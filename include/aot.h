@@ -68,6 +68,26 @@ typedef enum {
 #define AOT_ETA_DEG_DESC 0x0u /* degree non-increasing, ties by smaller id (default) */
 #define AOT_ETA_DEG_ASC 0x1u  /* degree non-decreasing, ties by smaller id           */
 #define AOT_FLAG_NO_LIST 0x2u /* size the workspace without the listing arrays      */
+/* Ablations of Sec. 4.2 ("More on AOT") and the charging of the baselines
+ * (Sec. 2.2, Sec. 2.3); counts and per-vertex counts never change:
+ *  AOT_FLAG_NO_CLIP      a negative item walks all of N+(u), as Algorithm 3
+ *                        prints it, instead of only the part after v.
+ *  AOT_FLAG_LOCAL_RANDOM AOT-randomOrder: every out-list in one fixed
+ *                        pseudo-random order (a bijection of the head rank)
+ *                        instead of the eta order; implies AOT_FLAG_NO_CLIP.
+ *                        Hubs then run on the global-bitmap path (hub_mode 1)
+ *                        whatever the tuning; only AOT_ROUTE_PLAIN and
+ *                        AOT_ROUTE_PROBE are accepted, and aot_list,
+ *                        aot_graph_features and the merge / binary-search
+ *                        cost recording return AOT_ERR_INVALID_ARG.
+ *  AOT_FLAG_TAIL_PIVOT   no adaptive orientation: every edge <u,v> is an item
+ *                        of its tail u walking all of N+(v).  With the probe
+ *                        route this is the work of kClist (Algorithm 2,
+ *                        sum of deg+(v)); with AOT_ROUTE_MERGE that of CF
+ *                        (Algorithm 1, sum of deg+(u) + deg+(v)). */
+#define AOT_FLAG_NO_CLIP 0x4u
+#define AOT_FLAG_LOCAL_RANDOM 0x8u
+#define AOT_FLAG_TAIL_PIVOT 0x10u
 
 /* Size limits: n < 2^31, num_edges < 2^40, oriented edges m < 2^32.  Larger
  * inputs return AOT_ERR_OVERFLOW. */
@@ -112,10 +132,28 @@ aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int64_t num_ed
 aot_status aot_graph_info(const aot_graph* g, int32_t* n, int64_t* m, uint64_t* work_w,
                           uint64_t* staged_s, int32_t* max_outdeg);
 
+/* Work counters of an oriented graph (cost model of Sec. 2.2, Sec. 2.3 and
+ * Sec. 3.2, for the graph's orientation flags):
+ *  walk        W, the summed walk length of the work items (probe route);
+ *  merge       W + sum over pivots of items(p) x deg+(p): the entries a
+ *              merge of every item's walk with N+(p) reads (merge route);
+ *  staged      S, as in aot_graph_info;
+ *  positive    items whose pivot is the tail of their edge;
+ *  items       all items (= m). */
+typedef struct {
+  uint64_t walk;
+  uint64_t merge;
+  uint64_t staged;
+  uint64_t positive;
+  uint64_t items;
+} aot_costs;
+aot_status aot_graph_costs(const aot_graph* g, aot_costs* out);
+
 /* Copy the orientation into caller buffers (any pointer may be NULL):
  * d_perm[n] (eta position -> original id), d_rank[n] (original id -> eta
  * position), d_out_off[n+1] (uint32 offsets of the out-CSR, rank space),
- * d_out_adj[m] (uint32 heads, ascending inside each list),
+ * d_out_adj[m] (uint32 heads, ascending inside each list; in the fixed
+ * pseudo-random order with AOT_FLAG_LOCAL_RANDOM),
  * d_items[n] (uint32 number of work items per pivot), d_walk[n] (uint64
  * summed walk length per pivot).  Ordered on s (no sync). */
 aot_status aot_graph_export(const aot_graph* g, int32_t* d_perm, int32_t* d_rank,

@@ -75,6 +75,10 @@ def _L():
         lib.og_stream_vertex_counts.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P,
                                                 ctypes.c_int32, P, P]
         lib.og_stream_vertex_counts.restype = ctypes.c_int
+        lib.og_work_rule.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+        lib.og_work_rule.restype = ctypes.c_int
+        lib.og_costs_noclip.argtypes = [P, ctypes.c_int, P]
+        lib.og_costs_noclip.restype = ctypes.c_int
         lib.og_threads.argtypes = [ctypes.c_int]
         lib.og_threads.restype = ctypes.c_int
         lib.og_new_par.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P, ctypes.POINTER(ctypes.c_int),
@@ -210,6 +214,23 @@ class Graph:
         if st:
             raise OracleError(st)
         return items, walk
+
+    def work_rule(self, rule: int, order: int = ORDER_DESC):
+        """Per-pivot items and walks for rule 0 (Algorithm 3 with the clip),
+        1 (Algorithm 3 as printed) or 2 (every edge walked from its tail)."""
+        items = np.empty(self.n, np.uint32)
+        walk = np.empty(self.n, np.uint64)
+        st = _L().og_work_rule(self._h, order, int(rule), items.ctypes.data, walk.ctypes.data)
+        if st:
+            raise OracleError(st)
+        return items, walk
+
+    def walk_noclip(self, order: int = ORDER_DESC) -> int:
+        out = np.zeros(1, np.uint64)
+        st = _L().og_costs_noclip(self._h, order, out.ctypes.data)
+        if st:
+            raise OracleError(st)
+        return int(out[0])
 
     def list_ids(self) -> np.ndarray:
         total = int(_L().og_list_ids(self._h, None, 0))

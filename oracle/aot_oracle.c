@@ -34,6 +34,11 @@
  *  og_work          Per-pivot item counts and walk sums of Algorithm 3
  *                   (positive: out-neighbour v with key(v) < key(u); negative:
  *                   in-neighbour x with key(x) < key(u); key = (deg+, rank)).
+ *  og_work_rule     The same for three charging rules: Algorithm 3 with the
+ *                   clip (= og_work), Algorithm 3 as printed (a negative edge
+ *                   walks all of N+(u)), and the charging of kClist / CF
+ *                   (Sec. 2.2, 2.3: every edge <u,v> walks N+(v) from u).
+ *  og_costs_noclip  W of Algorithm 3 as printed (no clip).
  *  og_list_canonical  Every triangle once as (x,y,z) with eta(x)<eta(y)<eta(z),
  *                   sorted lexicographically by (eta(x),eta(y),eta(z)), written
  *                   in original ids.
@@ -337,6 +342,55 @@ int og_work(const og_graph* g, int order, uint32_t* items, uint64_t* walk) {
       }
     }
   }
+  free(rk); free(pm); free(off); free(adj);
+  return OG_OK;
+}
+
+/* rule 0: Algorithm 3 with the clip; 1: without it; 2: every edge walks
+ * N+(v) from its tail u. */
+int og_work_rule(const og_graph* g, int order, int rule, uint32_t* items, uint64_t* walk) {
+  if (rule < 0 || rule > 2) return OG_ERR_ARG;
+  int32_t *rk, *pm, *adj;
+  int64_t* off;
+  int st = og_orient_alloc(g, order, &rk, &pm, &off, &adj);
+  if (st) return st;
+  memset(items, 0, (size_t)g->n * sizeof(uint32_t));
+  memset(walk, 0, (size_t)g->n * sizeof(uint64_t));
+  for (int32_t u = 0; u < g->n; ++u) {
+    for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+      int32_t v = adj[i];
+      if (rule == 2 || key_less(off, v, u)) { /* pivot u walks N+(v) */
+        items[u]++;
+        walk[u] += (uint64_t)(off[v + 1] - off[v]);
+      } else if (rule == 0) { /* pivot v walks N+(u) after v */
+        items[v]++;
+        walk[v] += (uint64_t)suffix_after(off, adj, u, v);
+      } else { /* pivot v walks all of N+(u) */
+        items[v]++;
+        walk[v] += (uint64_t)(off[u + 1] - off[u]);
+      }
+    }
+  }
+  free(rk); free(pm); free(off); free(adj);
+  return OG_OK;
+}
+
+/* W of Algorithm 3 without the clip: positive edges walk deg+(v), negative
+ * edges deg+(u). */
+int og_costs_noclip(const og_graph* g, int order, uint64_t* out) {
+  int32_t *rk, *pm, *adj;
+  int64_t* off;
+  int st = og_orient_alloc(g, order, &rk, &pm, &off, &adj);
+  if (st) return st;
+  uint64_t w = 0;
+  for (int32_t u = 0; u < g->n; ++u) {
+    uint64_t du = (uint64_t)(off[u + 1] - off[u]);
+    for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+      int32_t v = adj[i];
+      w += key_less(off, v, u) ? (uint64_t)(off[v + 1] - off[v]) : du;
+    }
+  }
+  *out = w;
   free(rk); free(pm); free(off); free(adj);
   return OG_OK;
 }

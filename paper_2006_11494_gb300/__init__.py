@@ -27,6 +27,9 @@ ROUTE_PLAIN, ROUTE_LEARNED, ROUTE_PROBE, ROUTE_MERGE, ROUTE_BSEARCH, ROUTE_RANDO
 ETA_DEG_DESC = 0x0
 ETA_DEG_ASC = 0x1
 FLAG_NO_LIST = 0x2
+FLAG_NO_CLIP = 0x4
+FLAG_LOCAL_RANDOM = 0x8
+FLAG_TAIL_PIVOT = 0x10
 
 _lib = None
 
@@ -38,6 +41,7 @@ SIGNATURES = {
     "aot_version": (ctypes.c_int, []),
     "aot_orient_workspace_size": (ctypes.c_int, [I64, I32, U32, ctypes.POINTER(SZ)]),
     "aot_orient": (ctypes.c_int, [P, P, I64, I32, U32, P, SZ, P, ctypes.POINTER(P)]),
+    "aot_graph_costs": (ctypes.c_int, [P, P]),
     "aot_graph_info": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I64),
                                       ctypes.POINTER(U64), ctypes.POINTER(U64),
                                       ctypes.POINTER(I32)]),
@@ -163,6 +167,18 @@ def aot_graph_info(handle: int) -> dict:
     _check(lib().aot_graph_info(handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(w),
                                 ctypes.byref(s), ctypes.byref(d)), "aot_graph_info")
     return {"n": n.value, "m": m.value, "W": w.value, "S": s.value, "max_outdeg": d.value}
+
+
+class Costs(ctypes.Structure):
+    """Mirror of aot_costs."""
+    _fields_ = [("walk", ctypes.c_uint64), ("merge", ctypes.c_uint64), ("staged", ctypes.c_uint64),
+                ("positive", ctypes.c_uint64), ("items", ctypes.c_uint64)]
+
+
+def aot_graph_costs(handle: int) -> dict:
+    c = Costs()
+    _check(lib().aot_graph_costs(handle, ctypes.byref(c)), "aot_graph_costs")
+    return {k: getattr(c, k) for k, _ in Costs._fields_}
 
 
 def aot_graph_export(handle: int, perm=None, rank=None, out_off=None, out_adj=None, items=None,

@@ -122,6 +122,16 @@ extern "C" aot_status aot_graph_info(const aot_graph* g, int32_t* n, int64_t* m,
   return AOT_OK;
 }
 
+extern "C" aot_status aot_graph_costs(const aot_graph* g, aot_costs* out) {
+  if (!g || !out) return AOT_ERR_INVALID_ARG;
+  out->walk = g->W;
+  out->merge = g->merge_work;
+  out->staged = g->S;
+  out->positive = g->positive;
+  out->items = (uint64_t)g->m;
+  return AOT_OK;
+}
+
 extern "C" aot_status aot_graph_export(const aot_graph* g, int32_t* d_perm, int32_t* d_rank,
                                        uint32_t* d_out_off, uint32_t* d_out_adj, uint32_t* d_items,
                                        uint64_t* d_walk, aot_stream_t stream) {

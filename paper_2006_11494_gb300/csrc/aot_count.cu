@@ -969,7 +969,10 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
       k_cta_pivots<MODE><<<(unsigned)grid, threads, smem, s>>>(P, ts_max);
     AOT_TRY(last_launch());
   }
-  if (nh && g->tune.hub_mode == 0) {
+  // the segmented sweep needs eta-sorted out-lists: a random local order
+  // takes the global bitmaps
+  const int hub_mode = (g->flags & AOT_FLAG_LOCAL_RANDOM) ? 1 : g->tune.hub_mode;
+  if (nh && hub_mode == 0) {
     // segmented shared-memory bitmap: tasks = (work group of a pivot, block
     // of SEG_ITEMS items), groups = tiles of the walked out-lists + negatives
     const uint32_t* dp = g->bin_pivots + nw + nc;
@@ -1107,6 +1110,9 @@ static aot_status reset_scalars(aot_graph* g, cudaStream_t s) {
 static aot_status check_route(aot_graph* g, aot_route route) {
   if (!g) return AOT_ERR_INVALID_ARG;
   if ((int)route < (int)AOT_ROUTE_PLAIN || (int)route > (int)AOT_ROUTE_RANDOM) return AOT_ERR_INVALID_ARG;
+  // merge and binary search need eta-sorted out-lists
+  if ((g->flags & AOT_FLAG_LOCAL_RANDOM) && route != AOT_ROUTE_PLAIN && route != AOT_ROUTE_PROBE)
+    return AOT_ERR_INVALID_ARG;
   if (route == AOT_ROUTE_LEARNED && !g->model) return AOT_ERR_NOT_READY;
   if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
   return AOT_OK;
@@ -1174,6 +1180,7 @@ extern "C" aot_status aot_graph_record_costs(aot_graph* g, int32_t variant, int3
                                              uint32_t* d_cycles, aot_stream_t stream) {
   if (!g || (g->m > 0 && !d_cycles) || variant < 0 || variant > 2) return AOT_ERR_INVALID_ARG;
   if (sample_log2 < 0 || sample_log2 > 30) return AOT_ERR_INVALID_ARG;
+  if ((g->flags & AOT_FLAG_LOCAL_RANDOM) && variant != V_PROBE) return AOT_ERR_INVALID_ARG;
   if (g->max_outdeg >= (1 << 27)) return AOT_ERR_OVERFLOW;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (g->m == 0) return AOT_OK;
@@ -1191,6 +1198,7 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
                                uint64_t cap, uint64_t* h_written, uint64_t* h_next, aot_stream_t stream) {
   AOT_TRY(check_route(g, route));
   if (!h_written || !h_next || (cap > 0 && !d_out)) return AOT_ERR_INVALID_ARG;
+  if (g->flags & AOT_FLAG_LOCAL_RANDOM) return AOT_ERR_INVALID_ARG;  // no canonical order
   if (!g->has_list) return AOT_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!g->list_ready) {

@@ -151,6 +151,8 @@ struct aot_graph {
   uint32_t flags = 0;
   int bits = 1;          // ceil(log2(n)), >= 1
   uint64_t W = 0, S = 0;
+  uint64_t merge_work = 0;  // W + sum over pivots of items x deg+ (merge route)
+  uint64_t positive = 0;    // items whose pivot is the tail of their edge
   int32_t max_outdeg = 0;
   // rank-space arrays in the workspace
   int32_t* perm = nullptr;   // n : eta position -> original id

@@ -457,6 +457,7 @@ extern "C" aot_status aot_mlp_train_step(void* d_model, float* d_master, float* 
 
 extern "C" aot_status aot_graph_features(aot_graph* g, float* d_feat, aot_stream_t stream) {
   if (!g || (g->m > 0 && !d_feat)) return AOT_ERR_INVALID_ARG;
+  if (g->flags & AOT_FLAG_LOCAL_RANDOM) return AOT_ERR_INVALID_ARG;  // suffix lengths need sorted lists
   if (g->m == 0) return AOT_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int T = 256;

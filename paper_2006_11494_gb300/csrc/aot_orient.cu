@@ -81,26 +81,49 @@ __global__ void k_rank_from_perm(const uint32_t* __restrict__ perm_sorted, int32
   degr[r] = deg[v];
 }
 
+// Random local order (AOT-randomOrder of Sec. 4.2): the out-lists are sorted
+// by a bijection h of the head rank on `bits`-bit words instead of the rank
+// itself, h(x) = ((x ^ (x >> sh)) * mul) mod 2^bits with mul odd, so every
+// list comes out in the same fixed pseudo-random order.  LocalOrder{0, 0}
+// is the identity (the eta local order of Sec. 3.2).
+struct LocalOrder {
+  uint32_t mul, inv;  // odd multiplier and its inverse mod 2^bits (0: identity)
+  int sh;
+};
+__device__ __forceinline__ uint32_t lo_hash(uint32_t x, const LocalOrder& o, uint32_t mask) {
+  return o.mul ? ((x ^ (x >> o.sh)) * o.mul) & mask : x;
+}
+__device__ __forceinline__ uint32_t lo_unhash(uint32_t y, const LocalOrder& o, uint32_t mask, int bits) {
+  if (!o.mul) return y;
+  uint32_t x = (y * o.inv) & mask;  // undo the multiplication, then the xor-shift
+  uint32_t r = x;
+  for (int k = o.sh; k < bits; k += o.sh) r = x ^ (r >> o.sh);
+  return r;
+}
+
 __global__ void k_relabel(const uint64_t* __restrict__ ukeys, int64_t m, int bits,
-                          const int32_t* __restrict__ rank, uint64_t* __restrict__ okeys) {
+                          const int32_t* __restrict__ rank, LocalOrder lo_ord,
+                          uint64_t* __restrict__ okeys) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
+  const uint32_t mask = (uint32_t)((1ull << bits) - 1);
   uint64_t k = ukeys[i];
   uint32_t a = (uint32_t)rank[(uint32_t)(k >> bits)];
-  uint32_t b = (uint32_t)rank[(uint32_t)(k & ((1ull << bits) - 1))];
+  uint32_t b = (uint32_t)rank[(uint32_t)(k & mask)];
   uint32_t lo = min(a, b), hi = max(a, b);
-  okeys[i] = ((uint64_t)lo << bits) | hi;
+  okeys[i] = ((uint64_t)lo << bits) | lo_hash(hi, lo_ord, mask);
 }
 
 __global__ void k_split_csr(const uint64_t* __restrict__ okeys, int64_t m, int bits,
-                            uint32_t* __restrict__ adj, uint32_t* __restrict__ esrc,
-                            uint32_t* __restrict__ outdeg) {
+                            LocalOrder lo_ord, uint32_t* __restrict__ adj,
+                            uint32_t* __restrict__ esrc, uint32_t* __restrict__ outdeg) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = i < m;
   uint64_t k = act ? okeys[i] : 0;
   uint32_t u = (uint32_t)(k >> bits);
   if (act) {
-    adj[i] = (uint32_t)(k & ((1ull << bits) - 1));
+    const uint32_t mask = (uint32_t)((1ull << bits) - 1);
+    adj[i] = lo_unhash((uint32_t)(k & mask), lo_ord, mask, bits);
     esrc[i] = u;
   }
   agg_inc(outdeg, u, act);
@@ -117,35 +140,46 @@ __device__ __forceinline__ bool key_less(uint32_t dx, uint32_t x, uint32_t dy, u
   return dx < dy || (dx == dy && x < y);
 }
 
+// Work item rules (orientation flags):
+//   RULE_AOT      Algorithm 3 with the suffix clip: a negative item walks
+//                 only the part of N+(u) after v (eta-sorted lists)
+//   RULE_NOCLIP   Algorithm 3 as printed: a negative item walks all of N+(u)
+//   RULE_TAIL     no adaptive choice: every edge is an item of its tail u
+//                 walking N+(v), the charging of Sec. 2.2 / Sec. 2.3 (with
+//                 the probe route the work of kClist, Algorithm 2, with the
+//                 merge route that of CF, Algorithm 1)
+enum ItemRule { RULE_AOT = 0, RULE_NOCLIP = 1, RULE_TAIL = 2 };
+
 // pivot of oriented edge e = <u,v> and its walk range
 __device__ __forceinline__ void edge_item(int64_t e, const uint32_t* __restrict__ esrc,
                                           const uint32_t* __restrict__ adj,
                                           const uint32_t* __restrict__ off,
-                                          const uint32_t* __restrict__ outdeg, uint32_t& pivot,
-                                          uint32_t& vert, uint2& range) {
+                                          const uint32_t* __restrict__ outdeg, int rule,
+                                          uint32_t& pivot, uint32_t& vert, uint2& range) {
   uint32_t u = esrc[e], v = adj[e];
   uint32_t du = outdeg[u], dv = outdeg[v];
-  if (key_less(dv, v, du, u)) {  // positive edge: pivot u walks N+(v)
+  if (rule == RULE_TAIL || key_less(dv, v, du, u)) {  // positive edge: pivot u walks N+(v)
     pivot = u;
     vert = v;
     range = make_uint2(off[v], off[v] + dv);
-  } else {  // negative edge: pivot v walks N+(u) after v
+  } else {  // negative edge: pivot v walks N+(u) (after v with the clip)
     pivot = v;
     vert = u;
-    range = make_uint2((uint32_t)e + 1, off[u] + du);
+    range = make_uint2(rule == RULE_AOT ? (uint32_t)e + 1 : off[u], off[u] + du);
   }
 }
 
 // items per pivot, and posflag[e] = 1 for a positive edge (its pivot is its tail)
 __global__ void k_item_count(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
                              const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
-                             int64_t m, uint32_t* __restrict__ items, uint32_t* __restrict__ posflag) {
+                             int64_t m, int rule, uint32_t* __restrict__ items,
+                             uint32_t* __restrict__ posflag) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = e < m;
   uint32_t p = 0, x;
   uint2 r;
   if (act) {
-    edge_item(e, esrc, adj, off, outdeg, p, x, r);
+    edge_item(e, esrc, adj, off, outdeg, rule, p, x, r);
     posflag[e] = p == esrc[e] ? 1u : 0u;
   }
   agg_inc(items, p, act);
@@ -157,7 +191,7 @@ __global__ void k_item_count(const uint32_t* __restrict__ esrc, const uint32_t* 
 // positive flags.  Negative items follow in arrival order (atomic cursor).
 __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* __restrict__ adj,
                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ outdeg,
-                            int64_t m, const uint32_t* __restrict__ wofs,
+                            int64_t m, int rule, const uint32_t* __restrict__ wofs,
                             const uint32_t* __restrict__ pscan, uint32_t* __restrict__ cursor,
                             uint2* __restrict__ witem, uint32_t* __restrict__ wvert,
                             uint32_t* __restrict__ wedge) {
@@ -167,7 +201,7 @@ __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* _
   uint2 r = make_uint2(0, 0);
   bool pos = false;
   if (act) {
-    edge_item(e, esrc, adj, off, outdeg, p, x, r);
+    edge_item(e, esrc, adj, off, outdeg, rule, p, x, r);
     pos = p == esrc[e];
   }
   const bool neg = act && !pos;
@@ -206,7 +240,11 @@ __global__ void k_pivot_walk(const uint32_t* __restrict__ wofs, const uint2* __r
   if (lane_id() == 0) {
     walk[p] = s;
     if (s) atomicAdd(&dev->total, (unsigned long long)s);
-    if (e > b) atomicAdd(&dev->aux[0], (unsigned long long)outdeg[p]);
+    if (e > b) {
+      atomicAdd(&dev->aux[0], (unsigned long long)outdeg[p]);
+      // a merge of each item's walk with N+(p) reads deg+(p) more entries
+      atomicAdd(&dev->aux[1], (unsigned long long)(e - b) * outdeg[p]);
+    }
   }
 }
 
@@ -375,10 +413,36 @@ static OrientLayout carve_orient(void* base, int64_t E, int32_t n, uint32_t flag
 
 using namespace aot;
 
+namespace aot {
+constexpr uint32_t ORIENT_FLAGS = AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST | AOT_FLAG_NO_CLIP |
+                                  AOT_FLAG_LOCAL_RANDOM | AOT_FLAG_TAIL_PIVOT;
+static bool flags_valid(uint32_t flags) {
+  if (flags & ~ORIENT_FLAGS) return false;
+  return true;
+}
+static int item_rule(uint32_t flags) {
+  if (flags & AOT_FLAG_TAIL_PIVOT) return RULE_TAIL;
+  if (flags & (AOT_FLAG_NO_CLIP | AOT_FLAG_LOCAL_RANDOM)) return RULE_NOCLIP;
+  return RULE_AOT;
+}
+// the fixed pseudo-random local order of AOT_FLAG_LOCAL_RANDOM on `bits`-bit ranks
+static LocalOrder local_order(uint32_t flags, int bits) {
+  LocalOrder o{0u, 0u, 1};
+  if (!(flags & AOT_FLAG_LOCAL_RANDOM)) return o;
+  const uint32_t mask = bits >= 32 ? 0xffffffffu : (uint32_t)((1ull << bits) - 1);
+  o.mul = (0x9E3779B9u & mask) | 1u;  // odd: a bijection mod 2^bits
+  uint32_t inv = o.mul;               // Newton's iteration for the inverse mod 2^32
+  for (int i = 0; i < 5; ++i) inv *= 2u - o.mul * inv;
+  o.inv = inv & mask;
+  o.sh = bits / 2 > 0 ? bits / 2 : 1;
+  return o;
+}
+}  // namespace aot
+
 extern "C" aot_status aot_orient_workspace_size(int64_t num_edges, int32_t num_vertices,
                                                 uint32_t flags, size_t* bytes) {
   if (!bytes || num_edges < 0 || num_vertices < 0) return AOT_ERR_INVALID_ARG;
-  if (flags & ~(AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST)) return AOT_ERR_INVALID_ARG;
+  if (!flags_valid(flags)) return AOT_ERR_INVALID_ARG;
   if (num_edges >= (int64_t(1) << 40)) return AOT_ERR_OVERFLOW;
   Tuning t;
   *bytes = carve_orient(nullptr, num_edges, num_vertices, flags, t).bytes;
@@ -392,7 +456,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   *out = nullptr;
   if (num_edges < 0 || num_vertices < 0) return AOT_ERR_INVALID_ARG;
   if (num_edges > 0 && (!d_src || !d_dst)) return AOT_ERR_INVALID_ARG;
-  if (flags & ~(AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST)) return AOT_ERR_INVALID_ARG;
+  if (!flags_valid(flags)) return AOT_ERR_INVALID_ARG;
   if (num_edges >= (int64_t(1) << 40)) return AOT_ERR_OVERFLOW;
   if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) return AOT_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -477,13 +541,14 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     uint64_t* ukeys = other;
     uint64_t* okeys = sorted;  // reuse the other buffer
     AOT_KERNEL("k_relabel", s)
-      k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, okeys);
+      k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, local_order(flags, bits), okeys);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     uint64_t* osorted;
     aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, s, &osorted);
     if (st) return fail(st);
     AOT_KERNEL("k_split_csr", s)
-      k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, L.adj, esrc, L.outdeg);
+      k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, local_order(flags, bits), L.adj, esrc,
+                                             L.outdeg);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
@@ -503,7 +568,8 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   uint32_t* pscan = L.pos;
   if (m > 0) {
     AOT_KERNEL("k_item_count", s)
-      k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.items, pscan);
+      k_item_count<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, item_rule(flags),
+                                              L.items, pscan);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     aot_status st = scan_u32_u32(pscan, pscan, m, L.tmp, s);
     if (st) return fail(st);
@@ -517,8 +583,8 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   }
   if (m > 0) {
     AOT_KERNEL("k_item_fill", s)
-      k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, L.wofs, pscan,
-                                             L.bin_flag, g->witem, g->wvert, g->wedge);
+      k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, item_rule(flags), L.wofs,
+                                             pscan, L.bin_flag, g->witem, g->wvert, g->wedge);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
@@ -528,12 +594,16 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   DevScalars hs;
+  uint32_t npos = 0;  // the positive-flag scan's total
   if (cudaMemcpyAsync(&hs, L.dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, s) ||
+      (m > 0 && cudaMemcpyAsync(&npos, pscan + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s)) ||
       cudaStreamSynchronize(s))
     return fail(AOT_ERR_CUDA);
+  g->positive = npos;
   if (hs.err) return fail(hs.err & DEVERR_RANGE ? AOT_ERR_VERTEX_RANGE : AOT_ERR_DEVICE_CHECK);
   g->W = hs.total;
   g->S = hs.aux[0];
+  g->merge_work = hs.total + hs.aux[1];
   g->max_outdeg = (int32_t)hs.counters[0];
   // 5. bins
   aot_status st = bin_pivots(g, s);

@@ -178,6 +178,79 @@ def test_asc_order_orientation_and_parity():
     assert g.info["W"] == ref.costs(oracle.ORDER_ASC)["walk"]
 
 
+@pytest.mark.parametrize("order", [oracle.ORDER_DESC, oracle.ORDER_ASC])
+@pytest.mark.parametrize("case", ["rmat", "chunglu"])
+def test_no_clip_and_tail_pivot(case, order):
+    """Algorithm 3 as printed (no suffix clip) and the tail charging of
+    kClist / CF: identical counts, per-vertex counts and canonical list; the
+    work counters equal the oracle's (W without the clip; sum of deg+(v) for
+    the tail rule, and sum of deg+(u) + deg+(v), CF's merge work, for its
+    merge route); per-pivot items and walks equal og_work_rule."""
+    import paper_2006_11494_gb300 as aot
+    if case == "rmat":
+        n, s, d = gg.rmat_cfg(13, 4)
+    else:
+        n = 1 << 12
+        s, d = gg.chunglu(n, 2.1, 24.0, seed=31)
+    eta = aot.ETA_DEG_ASC if order == oracle.ORDER_ASC else 0
+    ref = oracle.Graph(n, s, d)
+    c = ref.costs(order)
+    for flag, rule in ((aot.FLAG_NO_CLIP, 1), (aot.FLAG_TAIL_PIVOT, 2)):
+        g, _ = check_full(n, s, d, flags=eta | flag, order=order)
+        costs = aot.aot_graph_costs(g.handle)
+        if rule == 1:
+            assert costs["walk"] == ref.walk_noclip(order)
+            assert costs["positive"] == c["positive"]
+        else:
+            assert costs["walk"] == c["sum_deg_head"]
+            assert costs["merge"] == c["sum_cf"]
+            assert costs["positive"] == ref.m
+        ex = g.export()
+        oi, ow = ref.work_rule(rule, order)
+        assert np.array_equal(ex["items"].cpu().numpy().astype(np.uint32), oi)
+        assert np.array_equal(ex["walk"].cpu().numpy().astype(np.uint64), ow)
+
+
+@pytest.mark.parametrize("tuning", [None, dict(warp_max_outdeg=8, cta_max_outdeg=64)])
+def test_random_local_order(tuning):
+    """AOT-randomOrder (Sec. 4.2): out-lists in a fixed pseudo-random order,
+    negative items walk whole lists, hubs on the global bitmaps; counts and
+    per-vertex counts equal the oracle's, W equals the oracle's W without the
+    clip, the lists hold the same heads in another order, and the calls that
+    need sorted lists refuse."""
+    import torch
+    import paper_2006_11494_gb300 as aot
+    n, s, d = gg.rmat_cfg(13, 12)
+    ref = oracle.Graph(n, s, d)
+    T_ref, t_ref = ref.count_per_vertex()
+    g = gpu_graph(n, s, d, aot.FLAG_LOCAL_RANDOM)
+    if tuning:
+        g.set_tuning(**tuning)
+    assert g.count() == T_ref
+    T, t = g.count_per_vertex()
+    assert T == T_ref and np.array_equal(u64(t), t_ref)
+    assert g.count(aot.ROUTE_PROBE) == T_ref
+    assert aot.aot_graph_costs(g.handle)["walk"] == ref.walk_noclip()
+    rank, perm, off, adj = ref.orient()
+    ex = g.export()
+    gadj = ex["out_adj"].cpu().numpy().astype(np.int64)
+    assert np.array_equal(ex["out_off"].cpu().numpy().astype(np.int64), off)
+    unsorted = 0
+    for u in range(n):
+        a, b = off[u], off[u + 1]
+        assert np.array_equal(np.sort(gadj[a:b]), adj[a:b])
+        unsorted += int(not np.array_equal(gadj[a:b], adj[a:b]))
+    assert unsorted > n // 20
+    for route in (aot.ROUTE_MERGE, aot.ROUTE_BSEARCH, aot.ROUTE_RANDOM):
+        with pytest.raises(aot.AotError) as e:
+            g.count(route)
+        assert e.value.status == aot.ERR_INVALID_ARG
+    out = torch.empty(30, dtype=torch.int32, device="cuda")
+    with pytest.raises(aot.AotError) as e:
+        aot.aot_list(g.handle, aot.ROUTE_PLAIN, 0, out, 10)
+    assert e.value.status == aot.ERR_INVALID_ARG
+
+
 def test_hub_wheel():
     n, s, d = gg.wheel(20000)  # hub deg+ 20000: beyond the shared-memory bins
     g, ref = check_full(n, s, d)

@@ -227,10 +227,13 @@ def test_example1_costs():
 
 
 # -------------------------------------------- Algorithm 3, run literally
-def algorithm3(n, off, adj):
+def algorithm3(n, off, adj, clip=True, tail=False):
     """Algorithm 3 over an oriented CSR (rank space) with a global bitmap H.
     Ties of deg+ are broken by rank (footnote of the correctness argument);
-    the walk over N+(x) of a negative edge keeps the entries after the pivot.
+    with clip the walk over N+(x) of a negative edge keeps the entries after
+    the pivot, without it (as printed) it walks all of N+(x).  tail=True makes
+    every edge <u,v> positive (u walks N+(v)): the node iterator of kClist,
+    Algorithm 2, on the same orientation.
     Returns (triangles as rank triples, probes, per-pivot items, walks)."""
     outdeg = np.diff(off)
     ins = [[] for _ in range(n)]
@@ -246,7 +249,7 @@ def algorithm3(n, off, adj):
         Nu = adj[off[u]:off[u + 1]]
         H[Nu] = True
         for v in Nu:                          # positive edges <u,v>
-            if key(v) < key(u):
+            if tail or key(v) < key(u):
                 items[u] += 1
                 for w in adj[off[v]:off[v + 1]]:
                     probes += 1
@@ -254,10 +257,10 @@ def algorithm3(n, off, adj):
                     if H[w]:
                         found.append((u, v, w))
         for x in ins[u]:                      # negative edges <x,u>
-            if key(x) < key(u):
+            if not tail and key(x) < key(u):
                 items[u] += 1
                 for y in adj[off[x]:off[x + 1]]:
-                    if y <= u:
+                    if clip and y <= u:
                         continue
                     probes += 1
                     walks[u] += 1
@@ -298,6 +301,40 @@ def test_algorithm3_literal(case, order):
     assert np.array_equal(oi.astype(np.int64), items)
     assert np.array_equal(ow.astype(np.int64), walks)
     assert int(oi.sum()) == g.m
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+@pytest.mark.parametrize("case", ["er", "rmat", "wheel", "example1"])
+def test_algorithm3_rules_literal(case, rule):
+    """Algorithm 3 as printed (rule 1, no clip) and the tail charging of
+    kClist (rule 2): both find every triangle once; their probe counts equal
+    the oracle's og_costs_noclip / sum of deg+(v) and og_work_rule per pivot."""
+    if case == "er":
+        n = 150
+        s, d = random_graph(n, 1400, 22)
+    elif case == "rmat":
+        n, s, d = gg.rmat_cfg(8, seed=6)
+    elif case == "wheel":
+        n, s, d = gg.wheel(11)
+    else:
+        meta, s, d, _ = load_example1()
+        n = meta["n"]
+    g = oracle.Graph(n, s, d)
+    for order in (oracle.ORDER_DESC, oracle.ORDER_ASC):
+        rank, perm, off, adj = g.orient(order)
+        found, probes, items, walks = algorithm3(n, off, adj, clip=False, tail=rule == 2)
+        brute = brute_force(n, adjacency(n, s, d))
+        assert sorted(tuple(sorted(perm[list(t)])) for t in found) == brute
+        if rule == 1:
+            assert probes == g.walk_noclip(order) >= g.costs(order)["walk"]
+        else:
+            assert probes == g.costs(order)["sum_deg_head"]
+        oi, ow = g.work_rule(rule, order)
+        assert np.array_equal(oi.astype(np.int64), items)
+        assert np.array_equal(ow.astype(np.int64), walks)
+        ci, cw = g.work_rule(0, order)
+        wi, ww = g.work(order)
+        assert np.array_equal(ci, wi) and np.array_equal(cw, ww)
 
 
 def test_example1_walk():
