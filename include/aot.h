@@ -67,6 +67,13 @@ typedef enum {
 /* Orientation flags (aot_orient).  The global order eta of Sec. 1: */
 #define AOT_ETA_DEG_DESC 0x0u /* degree non-increasing, ties by smaller id (default) */
 #define AOT_ETA_DEG_ASC 0x1u  /* degree non-decreasing, ties by smaller id           */
+/* The degeneracy order that kClist orients by (Sec. 2.3, Algorithm 2), by
+ * peeling level by level: at level k every round removes all remaining
+ * vertices of current degree <= k at once, and k rises to the smallest
+ * remaining degree when none is left; eta = (removal round, id).  Every
+ * vertex then has at most its core number of later neighbours.  Not
+ * combinable with AOT_ETA_DEG_ASC. */
+#define AOT_ETA_DEGENERACY 0x20u
 #define AOT_FLAG_NO_LIST 0x2u /* size the workspace without the listing arrays      */
 /* Ablations of Sec. 4.2 ("More on AOT") and the charging of the baselines
  * (Sec. 2.2, Sec. 2.3); counts and per-vertex counts never change:

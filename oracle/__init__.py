@@ -25,6 +25,7 @@ _lib = None
 
 ORDER_DESC = 0  # eta: degree non-increasing, ties by smaller id
 ORDER_ASC = 1   # eta: degree non-decreasing, ties by smaller id
+ORDER_DEGEN = 2  # eta: degeneracy order (peeling round, then id)
 
 OK, ERR_ARG, ERR_RANGE, ERR_NOMEM = 0, 1, 2, 3
 
@@ -75,6 +76,8 @@ def _L():
         lib.og_stream_vertex_counts.argtypes = [ctypes.c_int32, ctypes.c_int64, P, P,
                                                 ctypes.c_int32, P, P]
         lib.og_stream_vertex_counts.restype = ctypes.c_int
+        lib.og_degeneracy.argtypes = [P, P, P]
+        lib.og_degeneracy.restype = ctypes.c_int
         lib.og_work_rule.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
         lib.og_work_rule.restype = ctypes.c_int
         lib.og_costs_noclip.argtypes = [P, ctypes.c_int, P]
@@ -224,6 +227,15 @@ class Graph:
         if st:
             raise OracleError(st)
         return items, walk
+
+    def degeneracy(self):
+        """(round[n], level[n]) of the level-by-level peeling; level = core number."""
+        rnd = np.empty(self.n, np.int32)
+        lvl = np.empty(self.n, np.int32)
+        st = _L().og_degeneracy(self._h, rnd.ctypes.data, lvl.ctypes.data)
+        if st:
+            raise OracleError(st)
+        return rnd, lvl
 
     def walk_noclip(self, order: int = ORDER_DESC) -> int:
         out = np.zeros(1, np.uint64)

@@ -22,6 +22,16 @@
  *                   non-increasing, ties by smaller id (footnote to the
  *                   correctness argument of Sec. 3.2).  ORDER_ASC is the
  *                   degree non-decreasing variant that Example 1 uses.
+ *                   ORDER_DEGEN is the degeneracy order that kClist orients
+ *                   by (Sec. 2.3, Algorithm 2), see og_degeneracy.
+ *  og_degeneracy    Core decomposition by peeling, level by level: at level
+ *                   k every round removes ALL remaining vertices of current
+ *                   degree <= k at once (their neighbours lose a degree per
+ *                   removed neighbour), and k rises to the smallest
+ *                   remaining degree when no vertex of degree <= k is left.
+ *                   round[v] = the round that removed v, level[v] = its k
+ *                   (the core number).  The degeneracy order is (round, id):
+ *                   every vertex has at most level[v] later neighbours.
  *  og_orient        Orientation (Algorithm 3, first step): <u,v> iff
  *                   eta(u) < eta(v); out-lists in eta order (the local order
  *                   of Sec. 3.2).  Reported in rank space (id -> eta rank).
@@ -77,6 +87,7 @@
 
 #define OG_ORDER_DESC 0
 #define OG_ORDER_ASC 1
+#define OG_ORDER_DEGEN 2
 
 typedef struct {
   int32_t n;
@@ -222,8 +233,77 @@ static int cmp_eta(const void* pa, const void* pb) {
   return (a > b) - (a < b);
 }
 
+static int cmp_u64(const void* a, const void* b);
+
+/* Peeling rounds and levels (see the header).  Returns OG_ERR_NOMEM or OG_OK. */
+int og_degeneracy(const og_graph* g, int32_t* round, int32_t* level) {
+  int32_t n = g->n;
+  int64_t* deg = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+  int32_t* rem = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t)); /* remaining vertices */
+  int32_t* fr = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));  /* this round's removals */
+  if (!deg || !rem || !fr) { free(deg); free(rem); free(fr); return OG_ERR_NOMEM; }
+  int32_t nrem = n, r = 0;
+  int64_t k = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    deg[v] = g->off[v + 1] - g->off[v];
+    rem[v] = v;
+    round[v] = -1;
+  }
+  while (nrem > 0) {
+    int32_t nf = 0, keep = 0;
+    for (int32_t i = 0; i < nrem; ++i) {
+      int32_t v = rem[i];
+      if (deg[v] <= k) fr[nf++] = v;
+      else rem[keep++] = v;
+    }
+    if (nf == 0) { /* next level: the smallest remaining degree */
+      k = deg[rem[0]];
+      for (int32_t i = 1; i < nrem; ++i)
+        if (deg[rem[i]] < k) k = deg[rem[i]];
+      continue;
+    }
+    for (int32_t i = 0; i < nf; ++i) {
+      round[fr[i]] = r;
+      level[fr[i]] = (int32_t)k;
+    }
+    for (int32_t i = 0; i < nf; ++i) {
+      int32_t v = fr[i];
+      for (int64_t j = g->off[v]; j < g->off[v + 1]; ++j)
+        if (round[g->adj[j]] < 0) deg[g->adj[j]]--;
+    }
+    nrem = keep;
+    ++r;
+  }
+  free(deg); free(rem); free(fr);
+  return OG_OK;
+}
+
+/* perm by ascending (round, id) of og_degeneracy */
+static int og_eta_degen(const og_graph* g, int32_t* rank, int32_t* perm) {
+  int32_t n = g->n;
+  int32_t* round = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  int32_t* level = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  uint64_t* key = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+  if (!round || !level || !key || og_degeneracy(g, round, level) != OG_OK) {
+    free(round); free(level); free(key);
+    return OG_ERR_NOMEM;
+  }
+  for (int32_t v = 0; v < n; ++v) key[v] = ((uint64_t)(uint32_t)round[v] << 32) | (uint32_t)v;
+  qsort(key, (size_t)n, sizeof(uint64_t), cmp_u64);
+  for (int32_t r = 0; r < n; ++r) {
+    perm[r] = (int32_t)(uint32_t)key[r];
+    rank[perm[r]] = r;
+  }
+  free(round); free(level); free(key);
+  return OG_OK;
+}
+
 /* perm[r] = vertex at eta position r, rank[v] = eta position of v. */
 void og_eta(const og_graph* g, int order, int32_t* rank, int32_t* perm) {
+  if (order == OG_ORDER_DEGEN) {
+    og_eta_degen(g, rank, perm);
+    return;
+  }
   for (int32_t v = 0; v < g->n; ++v) perm[v] = v;
   s_sort_g = g;
   s_sort_order = order;
@@ -568,6 +648,7 @@ og_graph* og_new_par(int32_t n, int64_t num_edges, const int32_t* src, const int
 
 /* eta as in og_eta, through a thread-safe sort of (degree key, id) words */
 static int og_eta_keys(const og_graph* g, int order, int32_t* rank, int32_t* perm) {
+  if (order == OG_ORDER_DEGEN) return og_eta_degen(g, rank, perm);
   int32_t n = g->n;
   uint64_t* key = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
   if (!key) return OG_ERR_NOMEM;

@@ -30,6 +30,7 @@ FLAG_NO_LIST = 0x2
 FLAG_NO_CLIP = 0x4
 FLAG_LOCAL_RANDOM = 0x8
 FLAG_TAIL_PIVOT = 0x10
+ETA_DEGENERACY = 0x20
 
 _lib = None
 

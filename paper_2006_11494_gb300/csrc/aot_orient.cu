@@ -70,6 +70,86 @@ __global__ void k_eta_keys(const uint32_t* __restrict__ deg, int32_t n, int bits
   ids[v] = (uint32_t)v;
 }
 
+// ---------------------------------------------- degeneracy order (peeling)
+// The degeneracy order of kClist (Sec. 2.3, Algorithm 2), computed level by
+// level: at level k each round removes every remaining vertex of current
+// degree <= k at once, and k rises to the smallest remaining degree when
+// none is left; eta = (round, id).  Every vertex then has at most its core
+// number of later neighbours.
+constexpr uint32_t UNSET = 0xffffffffu;
+
+// both directions of every unique edge, at the cursors of a copy of the offsets
+__global__ void k_sym_fill(const uint64_t* __restrict__ ukeys, int64_t m, int bits,
+                           uint32_t* __restrict__ cursor, uint32_t* __restrict__ sadj) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const uint64_t k = ukeys[i];
+  const uint32_t lo = (uint32_t)(k >> bits), hi = (uint32_t)(k & ((1ull << bits) - 1));
+  sadj[atomicAdd(&cursor[lo], 1u)] = hi;
+  sadj[atomicAdd(&cursor[hi], 1u)] = lo;
+}
+
+// warp-aggregated append of v to list[*cnt]
+__device__ __forceinline__ void warp_append(bool in, uint32_t v, uint32_t* list, unsigned int* cnt) {
+  const unsigned bal = __ballot_sync(FULL, in);
+  if (!bal) return;
+  const unsigned leader = (unsigned)(__ffs(bal) - 1);
+  uint32_t base = 0;
+  if (lane_id() == leader) base = atomicAdd(cnt, (unsigned)__popc(bal));
+  base = __shfl_sync(FULL, base, leader);
+  if (in) list[base + __popc(bal & lanemask_lt())] = v;
+}
+
+// the first frontier of level k: every remaining vertex of degree <= k
+__global__ void k_peel_scan(const uint32_t* __restrict__ cur, const uint32_t* __restrict__ rnd,
+                            int32_t n, uint32_t k, uint32_t* __restrict__ frontier, unsigned int* cnt) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = v < n && rnd[v] == UNSET && cur[v] <= k;
+  warp_append(in, (uint32_t)v, frontier, cnt);
+}
+
+// the smallest degree of a remaining vertex
+__global__ void k_peel_min(const uint32_t* __restrict__ cur, const uint32_t* __restrict__ rnd, int32_t n,
+                           unsigned int* out) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t d = v < n && rnd[v] == UNSET ? cur[v] : UNSET;
+  d = __reduce_min_sync(FULL, d);
+  if (lane_id() == 0 && d != UNSET) atomicMin(out, d);
+}
+
+// One round, a warp per frontier vertex v: round[v] = r, and every remaining
+// neighbour w loses one degree; the w whose degree drops from k+1 to k join
+// the next frontier (exactly one decrement sees that step).  A neighbour in
+// the same frontier may still read as remaining: its degree (already <= k)
+// only drops further and it is never appended again.
+__global__ void k_peel_round(const uint32_t* __restrict__ frontier, uint32_t nf, uint32_t r, uint32_t k,
+                             const uint32_t* __restrict__ soff, const uint32_t* __restrict__ sadj,
+                             uint32_t* __restrict__ cur, uint32_t* __restrict__ rnd,
+                             uint32_t* __restrict__ next, unsigned int* ncnt) {
+  const unsigned lane = lane_id();
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nf; f += warps) {
+    const uint32_t v = frontier[f];
+    if (lane == 0) rnd[v] = r;
+    const uint32_t b = soff[v], e = soff[v + 1];
+    for (uint32_t i0 = b; i0 < e; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      bool join = false;
+      uint32_t w = 0;
+      if (i < e) {
+        w = sadj[i];
+        if (rnd[w] == UNSET) join = atomicSub(&cur[w], 1u) == k + 1;
+      }
+      warp_append(join, w, next, ncnt);
+    }
+  }
+}
+
+__global__ void k_iota(uint32_t* __restrict__ a, int32_t n) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) a[v] = (uint32_t)v;
+}
+
 __global__ void k_rank_from_perm(const uint32_t* __restrict__ perm_sorted, int32_t n,
                                  const uint32_t* __restrict__ deg, int32_t* __restrict__ perm,
                                  int32_t* __restrict__ rank, uint32_t* __restrict__ degr) {
@@ -415,9 +495,10 @@ using namespace aot;
 
 namespace aot {
 constexpr uint32_t ORIENT_FLAGS = AOT_ETA_DEG_ASC | AOT_FLAG_NO_LIST | AOT_FLAG_NO_CLIP |
-                                  AOT_FLAG_LOCAL_RANDOM | AOT_FLAG_TAIL_PIVOT;
+                                  AOT_FLAG_LOCAL_RANDOM | AOT_FLAG_TAIL_PIVOT | AOT_ETA_DEGENERACY;
 static bool flags_valid(uint32_t flags) {
   if (flags & ~ORIENT_FLAGS) return false;
+  if ((flags & AOT_ETA_DEG_ASC) && (flags & AOT_ETA_DEGENERACY)) return false;  // one global order
   return true;
 }
 static int item_rule(uint32_t flags) {
@@ -437,6 +518,77 @@ static LocalOrder local_order(uint32_t flags, int bits) {
   o.sh = bits / 2 > 0 ? bits / 2 : 1;
   return o;
 }
+// Peeling rounds of the degeneracy order into L.ek0 (the eta sort keys).
+// Scratch: the symmetric adjacency in the dead cleanup keys (2m words of the
+// 8E bytes), its offsets in L.off and cursors in L.wofs, current degrees in
+// L.bin_flag, two frontiers in L.hubinfo, counters in the device scalars;
+// the later steps overwrite all of them.
+static aot_status degeneracy_rounds(aot_graph* g, const OrientLayout& L, const uint64_t* ukeys,
+                                    uint64_t* dead_keys, int64_t m, cudaStream_t s) {
+  const int T = 256;
+  const int32_t n = g->n;
+  uint32_t* soff = L.off;
+  uint32_t* cursor = L.wofs;
+  uint32_t* sadj = reinterpret_cast<uint32_t*>(dead_keys);
+  uint32_t* cur = L.bin_flag;
+  uint32_t* rnd = L.ek0;
+  uint32_t* fa = L.hubinfo;
+  uint32_t* fb = L.hubinfo + n;
+  unsigned int* cnt = &g->dev->counters[10];
+  unsigned int* kmin = &g->dev->counters[11];
+  AOT_TRY(scan_u32_u32(L.deg, soff, n, L.tmp, s));
+  if (m > 0) {
+    AOT_CUDA(cudaMemcpyAsync(cursor, soff, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    AOT_KERNEL("k_sym_fill", s)
+      k_sym_fill<<<grid_for(m, T), T, 0, s>>>(ukeys, m, g->bits, cursor, sadj);
+    AOT_TRY(last_launch());
+  }
+  AOT_CUDA(cudaMemcpyAsync(cur, L.deg, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  AOT_CUDA(cudaMemsetAsync(rnd, 0xff, sizeof(uint32_t) * n, s));
+  const int sms = sm_count();
+  uint32_t k = 0, r = 0;
+  int64_t remaining = n;
+  while (remaining > 0) {
+    unsigned int nf = 0;
+    AOT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), s));
+    AOT_KERNEL("k_peel_scan", s)
+      k_peel_scan<<<grid_for(n, T), T, 0, s>>>(cur, rnd, n, k, fa, cnt);
+    AOT_TRY(last_launch());
+    AOT_CUDA(cudaMemcpyAsync(&nf, cnt, sizeof(nf), cudaMemcpyDeviceToHost, s));
+    AOT_CUDA(cudaStreamSynchronize(s));
+    if (nf == 0) {  // next level: the smallest remaining degree
+      unsigned int km = UNSET;
+      AOT_CUDA(cudaMemsetAsync(kmin, 0xff, sizeof(unsigned int), s));
+      AOT_KERNEL("k_peel_min", s)
+        k_peel_min<<<grid_for(n, T), T, 0, s>>>(cur, rnd, n, kmin);
+      AOT_TRY(last_launch());
+      AOT_CUDA(cudaMemcpyAsync(&km, kmin, sizeof(km), cudaMemcpyDeviceToHost, s));
+      AOT_CUDA(cudaStreamSynchronize(s));
+      if (km == UNSET || km <= k) return AOT_ERR_DEVICE_CHECK;  // cannot happen: remaining > 0
+      k = km;
+      continue;
+    }
+    while (nf > 0) {
+      unsigned int nn = 0;
+      AOT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), s));
+      int64_t grid = ((int64_t)nf * 32 + T - 1) / T;
+      if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+      AOT_KERNEL("k_peel_round", s)
+        k_peel_round<<<(unsigned)grid, T, 0, s>>>(fa, nf, r, k, soff, sadj, cur, rnd, fb, cnt);
+      AOT_TRY(last_launch());
+      AOT_CUDA(cudaMemcpyAsync(&nn, cnt, sizeof(nn), cudaMemcpyDeviceToHost, s));
+      AOT_CUDA(cudaStreamSynchronize(s));
+      remaining -= nf;
+      ++r;
+      uint32_t* t = fa;
+      fa = fb;
+      fb = t;
+      nf = nn;
+    }
+  }
+  return AOT_OK;
+}
+
 }  // namespace aot
 
 extern "C" aot_status aot_orient_workspace_size(int64_t num_edges, int32_t num_vertices,
@@ -522,12 +674,20 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   g->m = m;
-  // 2. eta: stable sort of ids by degree key
-  if (n > 0) {
+  // 2. eta: stable sort of ids by degree key (or by peeling round)
+  if (n > 0 && (flags & AOT_ETA_DEGENERACY)) {
+    aot_status st = degeneracy_rounds(g, L, other, sorted, m, s);
+    if (st) return fail(st);
+    AOT_KERNEL("k_iota", s)
+      k_iota<<<grid_for(n, T), T, 0, s>>>(L.ev0, n);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+  } else if (n > 0) {
     AOT_KERNEL("k_eta_keys", s)
       k_eta_keys<<<grid_for(n, T), T, 0, s>>>(L.deg, n, bits, !(flags & AOT_ETA_DEG_ASC), L.ek0,
                                             L.ev0);
     if (last_launch()) return fail(AOT_ERR_CUDA);
+  }
+  if (n > 0) {
     uint32_t *ko, *vo;
     aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, s, &ko, &vo);
     if (st) return fail(st);

@@ -211,6 +211,49 @@ def test_no_clip_and_tail_pivot(case, order):
         assert np.array_equal(ex["walk"].cpu().numpy().astype(np.uint64), ow)
 
 
+@pytest.mark.parametrize("case", ["rmat12", "rmat15", "chunglu", "path", "star", "k30", "isolated"])
+def test_degeneracy_order(case):
+    """eta = the degeneracy order of kClist (Sec. 2.3), peeled on the GPU:
+    perm, rank and the out-CSR equal the oracle's, counts / per-vertex counts
+    / list too, and with the tail rule W is kClist's sum of deg+(v)."""
+    import paper_2006_11494_gb300 as aot
+    if case == "rmat12":
+        n, s, d = gg.rmat_cfg(12, 3)
+    elif case == "rmat15":
+        n, s, d = gg.rmat_cfg(15, 6)
+    elif case == "chunglu":
+        n = 5000
+        s, d = gg.chunglu(n, 2.1, 16.0, seed=17)
+    elif case == "path":
+        n = 1001
+        s, d = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+    elif case == "star":
+        n, s, d = gg.star(300)
+    elif case == "k30":
+        n, s, d = gg.complete(30)
+    else:
+        n, s, d = 50, np.array([3, 4, 5], np.int32), np.array([4, 5, 3], np.int32)
+    order = oracle.ORDER_DEGEN
+    g, ref = check_full(n, s, d, flags=aot.ETA_DEGENERACY, order=order)
+    rank, perm, off, adj = ref.orient(order)
+    ex = g.export()
+    assert np.array_equal(ex["perm"].cpu().numpy(), perm)
+    assert np.array_equal(ex["rank"].cpu().numpy(), rank)
+    assert np.array_equal(ex["out_off"].cpu().numpy().astype(np.int64), off)
+    assert np.array_equal(ex["out_adj"].cpu().numpy(), adj)
+    assert g.info["W"] == ref.costs(order)["walk"]
+    gt = gpu_graph(n, s, d, aot.ETA_DEGENERACY | aot.FLAG_TAIL_PIVOT)
+    assert aot.aot_graph_costs(gt.handle)["walk"] == ref.costs(order)["sum_deg_head"]
+    assert gt.count() == ref.count()
+
+
+def test_degeneracy_rejects_two_orders():
+    import paper_2006_11494_gb300 as aot
+    with pytest.raises(aot.AotError) as e:
+        aot.aot_orient_workspace_size(10, 5, aot.ETA_DEGENERACY | aot.ETA_DEG_ASC)
+    assert e.value.status == aot.ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("tuning", [None, dict(warp_max_outdeg=8, cta_max_outdeg=64)])
 def test_random_local_order(tuning):
     """AOT-randomOrder (Sec. 4.2): out-lists in a fixed pseudo-random order,

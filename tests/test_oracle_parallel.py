@@ -78,7 +78,7 @@ def test_closed_forms(case):
     assert len(g.list_canonical_par(oracle.ORDER_DESC, 2)) == T
 
 
-@pytest.mark.parametrize("order", [oracle.ORDER_DESC, oracle.ORDER_ASC])
+@pytest.mark.parametrize("order", [oracle.ORDER_DESC, oracle.ORDER_ASC, oracle.ORDER_DEGEN])
 def test_equals_serial_on_rmat(order):
     n, s, d = gg.rmat_cfg(14, 9)
     ref = oracle.Graph(n, s, d)

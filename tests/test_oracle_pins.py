@@ -415,3 +415,65 @@ def test_cost_identities(order):
     assert c["sum_deg_head"] == int((outd * ind).sum())
     assert c["sum_cf"] == int((outd * outd).sum()) + c["sum_deg_head"]
     assert c["walk"] <= c["sum_min"] <= c["sum_deg_head"]
+
+
+# ------------------------------------------------------ degeneracy order
+def _path(n):
+    return n, np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+
+
+@pytest.mark.parametrize("case", ["er", "rmat10", "chunglu", "wheel", "k9", "bip"])
+def test_degeneracy_levels_are_core_numbers(case):
+    """The peeling's level of every vertex is its core number (networkx's
+    core_number, an independent implementation); under the degeneracy order
+    every vertex has at most its core number of later neighbours, and the
+    largest out-degree is the degeneracy (Sec. 2.3: kClist orients by it)."""
+    nx = pytest.importorskip("networkx")
+    if case == "er":
+        n = 300
+        s, d = random_graph(n, 3000, 41)
+    elif case == "rmat10":
+        n, s, d = gg.rmat_cfg(10, seed=9)
+    elif case == "chunglu":
+        n = 2000
+        s, d = gg.chunglu(n, 2.1, 12.0, seed=3)
+    elif case == "wheel":
+        n, s, d = gg.wheel(20)
+    elif case == "k9":
+        n, s, d = gg.complete(9)
+    else:
+        n, s, d = gg.random_bipartite(40, 50, 0.2, 2)
+    g = oracle.Graph(n, s, d)
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from((int(a), int(b)) for a, b in zip(s, d) if a != b)
+    core = nx.core_number(G)
+    rnd, lvl = g.degeneracy()
+    assert all(lvl[v] == core[v] for v in range(n))
+    rank, perm, off, adj = g.orient(oracle.ORDER_DEGEN)
+    outdeg = np.diff(off)
+    assert np.all(outdeg[rank] <= lvl)
+    assert outdeg.max(initial=0) == max(core.values(), default=0)
+    # eta = (round, id)
+    key = rnd.astype(np.int64) * n + np.arange(n)
+    assert np.array_equal(perm, np.argsort(key, kind="stable"))
+    T, t = g.count_per_vertex()
+    assert len(g.list_canonical(oracle.ORDER_DEGEN)) == T
+
+
+def test_degeneracy_closed_forms():
+    # a path peels from both ends, one vertex per end per round (level 1)
+    n, s, d = _path(9)
+    rnd, lvl = oracle.Graph(n, s, d).degeneracy()
+    assert list(rnd) == [min(i, n - 1 - i) for i in range(n)] and set(lvl) == {1}
+    # a star: the leaves in round 0, then the centre (degree 0 by then)
+    n, s, d = gg.star(7)
+    rnd, lvl = oracle.Graph(n, s, d).degeneracy()
+    assert list(rnd) == [1] + [0] * 6 and list(lvl) == [1] * 7
+    # K_n: nothing at levels below n-1, then everything in one round
+    n, s, d = gg.complete(6)
+    rnd, lvl = oracle.Graph(n, s, d).degeneracy()
+    assert set(rnd) == {0} and set(lvl) == {5}
+    # isolated vertices first (level 0), then a triangle
+    rnd, lvl = oracle.Graph(5, np.array([2, 3, 4], np.int32), np.array([3, 4, 2], np.int32)).degeneracy()
+    assert list(rnd) == [0, 0, 1, 1, 1] and list(lvl) == [0, 0, 2, 2, 2]
