@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # The oracle (cleanup + parallel per-vertex count on every host core) runs on
 # the first 2^CPU_SAMPLE_LOG2 pairs of the benchmark's edge stream: the full
 # 2^28-pair graph takes minutes of host time, this prefix tens of seconds.
-CPU_SAMPLE_LOG2 = 26
+CPU_SAMPLE_LOG2 = 27
 
 # DRAM traffic per launch of the dominant kernel on the default workload, from
 # one ncu capture of this command's timed launch (dram__bytes_read.sum +
@@ -245,6 +245,48 @@ def bytes_per_kernel(info, bins, E, n):
     return out
 
 
+# The paper's algorithms and ablations on the same graph (Sec. 2.2, 2.3, 4.2):
+# (name, orientation flags, route, work counter that bounds it)
+VARIANTS = [
+    ("AOT, eta degree non-increasing (the benchmark)", 0, "ROUTE_PLAIN", "walk"),
+    ("AOT, eta degree non-decreasing", "ETA_DEG_ASC", "ROUTE_PLAIN", "walk"),
+    ("AOT, eta degeneracy", "ETA_DEGENERACY", "ROUTE_PLAIN", "walk"),
+    ("AOT without the suffix clip (Algorithm 3 as printed)", "FLAG_NO_CLIP", "ROUTE_PLAIN", "walk"),
+    ("AOT-randomOrder (random local order, Sec. 4.2)", "FLAG_LOCAL_RANDOM", "ROUTE_PLAIN", "walk"),
+    ("kClist work: degeneracy eta, every edge from its tail, index probe (Algorithm 2)",
+     "ETA_DEGENERACY|FLAG_TAIL_PIVOT", "ROUTE_PLAIN", "walk"),
+    ("kClist work on eta degree non-increasing", "FLAG_TAIL_PIVOT", "ROUTE_PLAIN", "walk"),
+    ("CF: degree non-decreasing eta, every edge from its tail, merge (Algorithm 1)",
+     "ETA_DEG_ASC|FLAG_TAIL_PIVOT", "ROUTE_MERGE", "merge"),
+]
+
+
+def variants(aot, src, dst, n, ws, stream, phase_ms, T_ref):
+    """Orientation time, work counter and count time of every variant; the
+    triangle count must equal the benchmark's."""
+    import torch
+    out = []
+    for name, flags, route, work in VARIANTS:
+        f = aot.FLAG_NO_LIST
+        if flags:
+            for part in flags.split("|"):
+                f |= getattr(aot, part)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h = aot.aot_orient(src, dst, n, f, ws, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c = aot.aot_graph_costs(h)
+        r = getattr(aot, route)
+        T = aot.aot_count(h, r, stream)
+        ms = phase_ms(lambda: aot.aot_count(h, r, stream), 2)
+        aot.aot_graph_destroy(h)
+        out.append({"variant": name, "orient_ms": e0.elapsed_time(e1), "work": work,
+                    "work_entries": c[work], "count_ms": ms, "same_T": T == T_ref})
+    return out
+
+
 def count_phase_bytes(info, n):
     """Algorithmic bytes of the whole count phase: stage N+(p) (4 S), the
     items (12 m: walk range and walked vertex), the walked entries (4 W), the
@@ -376,11 +418,7 @@ def run_ours(a):
                 "note": "model trained on R-MAT s18-22 timings; the plain rule judged it on a held-out graph"}
     aot.aot_graph_destroy(h)
     if not a.no_extras:
-        ha = aot.aot_orient(src, dst, n, aot.FLAG_NO_LIST | aot.ETA_DEG_ASC, ws, stream)
-        ia = aot.aot_graph_info(ha)
-        extras["ablation_eta_degree_ascending"] = {
-            "W": ia["W"], "count_only_ms": phase_ms(lambda: aot.aot_count(ha, aot.ROUTE_PLAIN, stream), a.steps)}
-        aot.aot_graph_destroy(ha)
+        extras["variants"] = variants(aot, src, dst, n, ws, stream, phase_ms, T)
 
     # end to end: pinned host edge list in, per-vertex counts out, every step
     e2e = None

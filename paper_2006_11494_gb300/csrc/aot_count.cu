@@ -363,6 +363,9 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
 // thread each, longer ones by a warp in rounds of 128 entries (256 while at
 // least seg_wide entries remain).  Each pivot's segment bounds (positions in
 // N+(p)) are precomputed once per call by k_seg_bounds.
+#ifndef AOT_PF_DIST
+#define AOT_PF_DIST 0
+#endif
 constexpr int SEG_THREADS = 1024;
 constexpr uint32_t SEG_ITEMS = 1536;
 
@@ -578,6 +581,13 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
   uint4 nxt[E / 4];
 #pragma unroll
   for (int q = 0; q < E / 4; ++q) nxt[q] = __ldg(src + q);
+#if AOT_PF_DIST > 0
+#pragma unroll
+  for (int dd = 1; dd <= AOT_PF_DIST; ++dd) {
+    const uint32_t pf = base + (uint32_t)dd * R + E * lane;
+    if (pf < y) asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + pf));
+  }
+#endif
   while (true) {
     uint32_t e[E];
 #pragma unroll
@@ -592,6 +602,10 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
     if (!fin) {  // the next round, only when the visit goes on
 #pragma unroll
       for (int q = 0; q < E / 4; ++q) nxt[q] = __ldg(src + 8 * E + q);
+#if AOT_PF_DIST > 0
+      const uint32_t pf = base + (uint32_t)(1 + AOT_PF_DIST) * R + E * lane;
+      if (pf < y) asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + pf));
+#endif
     }
     unsigned hits = 0;
 #pragma unroll

@@ -131,7 +131,7 @@ struct Tuning {
   uint32_t seg_bits = 1536u * 1024u;  // ranks per shared-memory bitmap segment (hub_mode 0)
   uint32_t seg_wide = 512;            // hub_mode 0: warp walks take rounds of 256 while this many entries remain
   uint32_t seg_long = 128;            // hub_mode 0: items this long walked warp-wide, shorter ones per thread
-  uint32_t tile_bits = 23;            // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
+  uint32_t tile_bits = 0;             // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
 };
 
 struct DevScalars {  // small device-resident scalars

@@ -152,6 +152,34 @@ def test_rmat20_full_size(aot):
     assert stream_list_exact(aot, g, 1 << 26, ref_list) == T_ref
 
 
+def test_rmat20_variant_work_counters(aot):
+    """Config 2: the work counters of AOT's orders and ablations and of the
+    kClist / CF charging equal the oracle's cost counters exactly (Sec. 2.2,
+    2.3, 3.2), and every variant counts the same triangles."""
+    import torch
+    n, s, d = gg.rmat_cfg(20, 2)
+    ref = oracle.Graph(n, s, d, threads=0)
+    T_ref = ref.count_par()
+    src, dst = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    cost = {o: ref.costs(o) for o in (oracle.ORDER_DESC, oracle.ORDER_ASC, oracle.ORDER_DEGEN)}
+    cases = [
+        (0, "walk", cost[oracle.ORDER_DESC]["walk"]),
+        (aot.ETA_DEG_ASC, "walk", cost[oracle.ORDER_ASC]["walk"]),
+        (aot.ETA_DEGENERACY, "walk", cost[oracle.ORDER_DEGEN]["walk"]),
+        (aot.FLAG_NO_CLIP, "walk", ref.walk_noclip(oracle.ORDER_DESC)),
+        (aot.FLAG_LOCAL_RANDOM, "walk", ref.walk_noclip(oracle.ORDER_DESC)),
+        (aot.FLAG_TAIL_PIVOT, "walk", cost[oracle.ORDER_DESC]["sum_deg_head"]),
+        (aot.ETA_DEGENERACY | aot.FLAG_TAIL_PIVOT, "walk", cost[oracle.ORDER_DEGEN]["sum_deg_head"]),
+        (aot.ETA_DEG_ASC | aot.FLAG_TAIL_PIVOT, "merge", cost[oracle.ORDER_ASC]["sum_cf"]),
+    ]
+    for flags, key, want in cases:
+        g = aot.OrientedGraph(src, dst, n, flags | aot.FLAG_NO_LIST)
+        assert aot.aot_graph_costs(g.handle)[key] == want, (flags, key)
+        route = aot.ROUTE_MERGE if key == "merge" else aot.ROUTE_PLAIN
+        assert g.count(route) == T_ref, flags
+        g.close()
+
+
 def test_rmat24_full_counts_and_streamed_listing(aot):
     rng = np.random.default_rng(24)
     n, s, d = gg.rmat_cfg(24, 3)
