@@ -380,15 +380,29 @@ aot_status aot_batch_workspace_size(int64_t total_edges, int32_t num_graphs, int
  * sum of d_nv).  Output: d_tri[g] (uint64) and d_vcount[voff[g] + v] = t(v)
  * (uint64) with voff the exclusive prefix of d_nv.  The batch is processed as
  * the disjoint union of its graphs (one orientation, one set of persistent
- * bin kernels); the counting phase is captured into a CUDA graph and
- * launched when s is a created stream that is not already capturing (else
- * its kernels are launched on s directly).  Synchronises s.
+ * bin kernels, the process default tuning); the counting phase is captured
+ * into a CUDA graph and launched when s is a created stream that is not
+ * already capturing (else its kernels are launched on s directly).  Each
+ * host thread keeps its last instantiated graph per device and updates it in
+ * place for the next call whose captured kernels match (the orientation, with
+ * its host synchronisations, always runs outside the graph).  Synchronises s.
  * Errors: AOT_ERR_INVALID_ARG for inconsistent offsets or counts,
  * AOT_ERR_VERTEX_RANGE if an id lies outside its own graph. */
 aot_status aot_batch(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
                      const int32_t* d_nv, int32_t num_graphs, int64_t total_edges,
                      int64_t total_vertices, aot_route route, uint64_t* d_tri, uint64_t* d_vcount,
                      void* d_ws, size_t ws_bytes, aot_stream_t s);
+
+/* Autotuner for batches: builds the union graph of the batch exactly as
+ * aot_batch does and runs aot_tune on it in per-vertex mode (reps timings
+ * per candidate); the best tuning is returned in *best_out (hub_mode 0) and
+ * its time in *h_best_ms (may be NULL).  Install it with
+ * aot_set_default_tuning before aot_batch, which takes the default tuning.
+ * Arguments as for aot_batch; the same workspace size.  Synchronises s. */
+aot_status aot_batch_tune(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
+                          const int32_t* d_nv, int32_t num_graphs, int64_t total_edges,
+                          int64_t total_vertices, int32_t reps, aot_tuning* best_out,
+                          float* h_best_ms, void* d_ws, size_t ws_bytes, aot_stream_t s);
 
 /* Free the host handle (the workspace stays with the caller). */
 aot_status aot_graph_destroy(aot_graph* g);

@@ -69,6 +69,7 @@ SIGNATURES = {
     "aot_set_default_router": (ctypes.c_int, [P]),
     "aot_batch_workspace_size": (ctypes.c_int, [I64, I32, I64, ctypes.POINTER(SZ)]),
     "aot_batch": (ctypes.c_int, [P, P, P, P, I32, I64, I64, ctypes.c_int, P, P, P, SZ, P]),
+    "aot_batch_tune": (ctypes.c_int, [P, P, P, P, I32, I64, I64, I32, P, P, P, SZ, P]),
     "aot_kernel_launches": (ctypes.c_ulonglong, []),
     "aot_profile_begin": (ctypes.c_int, []),
     "aot_profile_end": (ctypes.c_int, [P, I32, ctypes.POINTER(I32)]),
@@ -347,6 +348,21 @@ def aot_batch(src, dst, edge_ofs, nv, route, tri, vcount, workspace, total_verti
                            route, _ptr(tri), _ptr(vcount) if total_vertices > 0 else None,
                            _ptr(workspace), workspace.numel() * workspace.element_size(),
                            _stream(stream)), "aot_batch")
+
+
+def aot_batch_tune(src, dst, edge_ofs, nv, workspace, total_vertices=None, reps: int = 1, stream=None):
+    """Autotuned tuning of a batch's union graph: (Tuning, best ms)."""
+    G = nv.numel()
+    E = src.numel()
+    if total_vertices is None:
+        total_vertices = int(nv.sum().item())
+    t = Tuning()
+    ms = ctypes.c_float(0)
+    _check(lib().aot_batch_tune(_ptr(src), _ptr(dst), _ptr(edge_ofs), _ptr(nv), G, E, total_vertices,
+                                reps, ctypes.byref(t), ctypes.byref(ms), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)),
+           "aot_batch_tune")
+    return t, ms.value
 
 
 def aot_graph_destroy(handle: int):

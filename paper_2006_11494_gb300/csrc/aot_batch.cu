@@ -8,7 +8,12 @@
 // orientation covers the whole batch (its radix sorts see all graphs at
 // once), and the counting phase -- the persistent bin kernels with their
 // atomic work queues and the per-graph totals -- is captured into a CUDA
-// graph and launched once.
+// graph and launched once.  Each host thread keeps its last instantiated
+// graph per device and updates it in place (cudaGraphExecUpdate) when the
+// next batch captures the same sequence of kernels, so repeated calls of one
+// shape pay no instantiation.
+#include <map>
+
 #include "aot_internal.cuh"
 
 namespace aot {
@@ -83,6 +88,87 @@ static aot_status carve_batch(void* base, int64_t E, int32_t G, int64_t N, Batch
   return AOT_OK;
 }
 
+// The calling thread's instantiated counting graph on each device.
+struct ExecCache {
+  std::map<int, cudaGraphExec_t> exec;
+  ~ExecCache() {
+    for (auto& kv : exec) cudaGraphExecDestroy(kv.second);
+  }
+};
+static thread_local ExecCache t_exec;
+
+// Launch a captured graph through the thread's cached executable (updated in
+// place when the kernels match, else re-instantiated).
+static aot_status launch_captured(cudaGraph_t graph, cudaStream_t s) {
+  int dev = 0;
+  AOT_CUDA(cudaGetDevice(&dev));
+  cudaGraphExec_t& ex = t_exec.exec[dev];
+  if (ex) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ex, graph, &info) != cudaSuccess) {
+      cudaGetLastError();  // an update that does not fit is not an error: re-instantiate
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+  }
+  if (!ex && cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+    ex = nullptr;
+    return AOT_ERR_CUDA;
+  }
+  AOT_CUDA(cudaGraphLaunch(ex, s));
+  return AOT_OK;
+}
+
+// Union graph of a batch, oriented (shared by aot_batch and aot_batch_tune).
+static aot_status batch_union(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
+                              const int32_t* d_nv, int32_t G, int64_t E, int64_t N, const BatchLayout& L,
+                              cudaStream_t s, aot_graph** out) {
+  const int T = 256;
+  AOT_CUDA(cudaMemsetAsync(L.err, 0, sizeof(uint32_t), s));
+  AOT_TRY(scan_u32_u32(reinterpret_cast<const uint32_t*>(d_nv), L.voff, G, L.scan_tmp, s));
+  AOT_KERNEL("k_batch_check", s)
+    k_batch_check<<<(unsigned)((G + 1 + T - 1) / T), T, 0, s>>>(d_edge_ofs, G, E, d_nv, L.voff, N, L.err);
+  AOT_TRY(last_launch());
+  uint32_t herr = 0;
+  AOT_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AOT_CUDA(cudaStreamSynchronize(s));
+  if (herr) return AOT_ERR_INVALID_ARG;
+  if (E > 0) {
+    AOT_KERNEL("k_batch_ids", s)
+      k_batch_ids<<<(unsigned)((E + T - 1) / T), T, 0, s>>>(d_src, d_dst, E, d_edge_ofs, G, d_nv,
+                                                           L.voff, L.gsrc, L.gdst, L.err);
+    AOT_TRY(last_launch());
+  }
+  // one orientation of the union graph (synchronises s)
+  aot_graph* g = nullptr;
+  AOT_TRY(aot_orient(L.gsrc, L.gdst, E, (int32_t)N, AOT_FLAG_NO_LIST, L.orient_ws, L.orient_bytes,
+                     reinterpret_cast<aot_stream_t>(s), &g));
+  if (g->tune.hub_mode != 0) {  // the global-bitmap hub path reads hub descriptors on the host
+    aot_tuning t;
+    aot_graph_get_tuning(g, &t);
+    t.hub_mode = 0;
+    aot_status st = aot_graph_set_tuning(g, &t, reinterpret_cast<aot_stream_t>(s));
+    if (st != AOT_OK) {
+      aot_graph_destroy(g);
+      return st;
+    }
+  }
+  *out = g;
+  return AOT_OK;
+}
+
+static aot_status batch_args(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
+                             const int32_t* d_nv, int32_t G, int64_t E, int64_t N, void* d_ws,
+                             size_t ws_bytes, BatchLayout* L) {
+  if (G < 0 || E < 0 || N < 0) return AOT_ERR_INVALID_ARG;
+  if (!d_edge_ofs || !d_nv || (E > 0 && (!d_src || !d_dst))) return AOT_ERR_INVALID_ARG;
+  if (N >= (int64_t(1) << 31)) return AOT_ERR_OVERFLOW;
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return AOT_ERR_WORKSPACE;
+  AOT_TRY(carve_batch(d_ws, E, G, N, L));
+  if (ws_bytes < L->bytes) return AOT_ERR_WORKSPACE;
+  return AOT_OK;
+}
+
 }  // namespace aot
 
 using namespace aot;
@@ -103,48 +189,16 @@ extern "C" aot_status aot_batch(const int32_t* d_src, const int32_t* d_dst, cons
                                 uint64_t* d_vcount, void* d_ws, size_t ws_bytes, aot_stream_t stream) {
   if (num_graphs < 0 || total_edges < 0 || total_vertices < 0) return AOT_ERR_INVALID_ARG;
   if (num_graphs == 0) return AOT_OK;
-  if (!d_edge_ofs || !d_nv || !d_tri || (total_edges > 0 && (!d_src || !d_dst)) ||
-      (total_vertices > 0 && !d_vcount))
-    return AOT_ERR_INVALID_ARG;
-  if (total_vertices >= (int64_t(1) << 31)) return AOT_ERR_OVERFLOW;
-  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return AOT_ERR_WORKSPACE;
+  if (!d_tri || (total_vertices > 0 && !d_vcount)) return AOT_ERR_INVALID_ARG;
   BatchLayout L;
-  AOT_TRY(carve_batch(d_ws, total_edges, num_graphs, total_vertices, &L));
-  if (ws_bytes < L.bytes) return AOT_ERR_WORKSPACE;
+  AOT_TRY(batch_args(d_src, d_dst, d_edge_ofs, d_nv, num_graphs, total_edges, total_vertices, d_ws,
+                     ws_bytes, &L));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int T = 256;
   const int32_t G = num_graphs;
-  const int64_t E = total_edges, N = total_vertices;
-  // vertex offsets and input checks
-  AOT_CUDA(cudaMemsetAsync(L.err, 0, sizeof(uint32_t), s));
-  AOT_TRY(scan_u32_u32(reinterpret_cast<const uint32_t*>(d_nv), L.voff, G, L.scan_tmp, s));
-  AOT_KERNEL("k_batch_check", s)
-    k_batch_check<<<(unsigned)((G + 1 + T - 1) / T), T, 0, s>>>(d_edge_ofs, G, E, d_nv, L.voff, N, L.err);
-  AOT_TRY(last_launch());
-  uint32_t herr = 0;
-  AOT_CUDA(cudaMemcpyAsync(&herr, L.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  AOT_CUDA(cudaStreamSynchronize(s));
-  if (herr) return AOT_ERR_INVALID_ARG;
-  if (E > 0) {
-    AOT_KERNEL("k_batch_ids", s)
-      k_batch_ids<<<(unsigned)((E + T - 1) / T), T, 0, s>>>(d_src, d_dst, E, d_edge_ofs, G, d_nv,
-                                                           L.voff, L.gsrc, L.gdst, L.err);
-    AOT_TRY(last_launch());
-  }
-  // one orientation of the union graph (synchronises s)
+  const int64_t N = total_vertices;
   aot_graph* g = nullptr;
-  AOT_TRY(aot_orient(L.gsrc, L.gdst, E, (int32_t)N, AOT_FLAG_NO_LIST, L.orient_ws, L.orient_bytes,
-                     stream, &g));
-  if (g->tune.hub_mode != 0) {  // the global-bitmap hub path reads hub descriptors on the host
-    aot_tuning t;
-    aot_graph_get_tuning(g, &t);
-    t.hub_mode = 0;
-    aot_status st = aot_graph_set_tuning(g, &t, stream);
-    if (st != AOT_OK) {
-      aot_graph_destroy(g);
-      return st;
-    }
-  }
+  AOT_TRY(batch_union(d_src, d_dst, d_edge_ofs, d_nv, G, total_edges, N, L, s, &g));
   // counting phase, captured into a CUDA graph when the stream allows it
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool capture = s != nullptr && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
@@ -161,16 +215,28 @@ extern "C" aot_status aot_batch(const int32_t* d_src, const int32_t* d_dst, cons
   if (capture) {
     const cudaError_t ec = cudaStreamEndCapture(s, &graph);
     if (st == AOT_OK && ec != cudaSuccess) st = AOT_ERR_CUDA;
-    if (st == AOT_OK) {
-      cudaGraphExec_t exec = nullptr;
-      if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = AOT_ERR_CUDA;
-      if (st == AOT_OK && cudaGraphLaunch(exec, s) != cudaSuccess) st = AOT_ERR_CUDA;
-      if (exec) cudaGraphExecDestroy(exec);
-    }
+    if (st == AOT_OK) st = launch_captured(graph, s);
     if (graph) cudaGraphDestroy(graph);
   }
   if (st == AOT_OK && cudaStreamSynchronize(s) != cudaSuccess) st = AOT_ERR_CUDA;
   if (st == AOT_OK) st = read_device_error(g, s);
+  aot_graph_destroy(g);
+  return st;
+}
+
+extern "C" aot_status aot_batch_tune(const int32_t* d_src, const int32_t* d_dst, const int64_t* d_edge_ofs,
+                                     const int32_t* d_nv, int32_t num_graphs, int64_t total_edges,
+                                     int64_t total_vertices, int32_t reps, aot_tuning* best_out,
+                                     float* h_best_ms, void* d_ws, size_t ws_bytes, aot_stream_t stream) {
+  if (num_graphs <= 0 || !best_out) return AOT_ERR_INVALID_ARG;
+  BatchLayout L;
+  AOT_TRY(batch_args(d_src, d_dst, d_edge_ofs, d_nv, num_graphs, total_edges, total_vertices, d_ws,
+                     ws_bytes, &L));
+  aot_graph* g = nullptr;
+  AOT_TRY(batch_union(d_src, d_dst, d_edge_ofs, d_nv, num_graphs, total_edges, total_vertices, L,
+                      reinterpret_cast<cudaStream_t>(stream), &g));
+  aot_status st = aot_tune(g, 1, reps, best_out, h_best_ms, stream);
+  if (st == AOT_OK) best_out->hub_mode = 0;  // batches keep the hubs on the segmented bitmap
   aot_graph_destroy(g);
   return st;
 }

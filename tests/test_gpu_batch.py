@@ -90,6 +90,19 @@ def test_batch_on_default_and_side_streams(aot):
     check_against_oracle(graphs, *a)
 
 
+def test_batch_graph_reused_across_calls(aot):
+    """Several batches in a row on one stream: the thread's instantiated
+    counting graph is updated in place (same kernels) or rebuilt (different
+    ones); every result matches the oracle."""
+    import torch
+    st = torch.cuda.Stream()
+    graphs = small_graphs()
+    for part in (graphs[:10], graphs[10:20], graphs[:10], graphs[20:], graphs):
+        batch = make_batch(part)
+        tri, vc = run_batch(aot, batch, 0, st)
+        check_against_oracle(part, tri, vc)
+
+
 def test_batch_rejects_bad_input(aot):
     import torch
     graphs = [gg.complete(4), gg.complete(5)]
@@ -123,13 +136,22 @@ def oracle_counts_threaded(graphs):
 
 def test_batch_of_4096_chunglu_graphs(aot):
     """4096 Chung-Lu graphs (n log-uniform in [256, 65536], mean degree
-    uniform in [4, 64], gamma 2.5): every graph's T and t(v) against the
-    oracle."""
+    uniform in [4, 64], gamma 2.5), with the tuning the batch autotuner picks
+    on their union graph: every graph's T and t(v) against the oracle."""
     import torch
     nv, ofs, s, d = gg.batch(4096)
     batch = (torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(ofs).cuda(),
              torch.from_numpy(nv).cuda(), nv, ofs)
-    tri, vc = run_batch(aot, batch, 0, torch.cuda.Stream())
+    G, N = len(nv), int(nv.sum())
+    ws = torch.empty(aot.aot_batch_workspace_size(len(s), G, N), dtype=torch.uint8, device="cuda")
+    best, ms = aot.aot_batch_tune(batch[0], batch[1], batch[2], batch[3], ws, N)
+    assert ms > 0 and best.hub_mode == 0
+    old = aot.aot_get_default_tuning()
+    try:
+        aot.aot_set_default_tuning(best)
+        tri, vc = run_batch(aot, batch, 0, torch.cuda.Stream())
+    finally:
+        aot.aot_set_default_tuning(old)
     graphs = [(int(nv[i]), s[ofs[i]:ofs[i + 1]], d[ofs[i]:ofs[i + 1]]) for i in range(len(nv))]
     ref = oracle_counts_threaded(graphs)
     voff = np.concatenate([[0], np.cumsum(nv.astype(np.int64))])
