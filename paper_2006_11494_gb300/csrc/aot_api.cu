@@ -25,6 +25,20 @@ aot_status ensure_dyn_smem(const void* func, size_t bytes) {
   return AOT_OK;
 }
 
+static std::map<std::pair<int, const void*>, bool> g_carveout;  // (device, kernel) set
+
+aot_status prefer_max_smem(const void* func) {
+  int dev = 0;
+  AOT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  bool& done = g_carveout[std::make_pair(dev, func)];
+  if (done) return AOT_OK;
+  AOT_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
+  done = true;
+  return AOT_OK;
+}
+
 int sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;

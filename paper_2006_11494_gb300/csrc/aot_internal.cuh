@@ -39,6 +39,9 @@ inline aot_status last_launch() {
 // largest value set so far is remembered per (device, kernel), under a mutex
 // (calls may come from several host threads and devices).
 aot_status ensure_dyn_smem(const void* func, size_t bytes);
+// Ask for the largest shared-memory carveout for kernel `func` on the current
+// device (once per device and kernel), so that several of its blocks fit.
+aot_status prefer_max_smem(const void* func);
 // Streaming multiprocessors of the current device (cached per device).
 int sm_count();
 

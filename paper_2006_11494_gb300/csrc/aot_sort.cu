@@ -142,23 +142,27 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__
                                                            int64_t tiles) {
   __shared__ uint32_t h[RS_BUCKETS];
   h[threadIdx.x] = 0;
-  __syncthreads();
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   int64_t base = (int64_t)blockIdx.x * RS_TILE + warp * RS_WARP_KEYS;
-#pragma unroll 4
+  unsigned dig[RS_ROUNDS];  // every load of the lane in flight before the first ranking
+#pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t idx = base + r * 32 + lane;
-    bool valid = idx < N;
-    unsigned d = valid ? (unsigned)((keys[idx] >> shift) & 0xFF) : 0x100u;
+    dig[r] = idx < N ? (unsigned)((__ldcs(keys + idx) >> shift) & 0xFF) : 0x100u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const unsigned d = dig[r];
     unsigned peers = __match_any_sync(FULL, d);
-    if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    if (d < 0x100u && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
 template <class K, bool VALS>
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin,
                                                               int64_t N, int shift,
                                                               const uint32_t* __restrict__ offs,
@@ -181,13 +185,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
   const int64_t base = tile_base + warp * RS_WARP_KEYS;
   K key[RS_ROUNDS];
   uint32_t val[RS_ROUNDS];
-  uint32_t lrank[RS_ROUNDS];
+  uint32_t lrk[RS_ROUNDS / 2];  // local ranks (< 512), two 16-bit halves per word
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {  // every load of the lane in flight first
+    int64_t idx = base + r * 32 + lane;
+    bool valid = idx < N;
+    key[r] = valid ? __ldcs(kin + idx) : K(0);
+    if (VALS) val[r] = valid ? __ldcs(vin + idx) : 0u;
+  }
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t idx = base + r * 32 + lane;
     bool valid = idx < N;
-    key[r] = valid ? kin[idx] : K(0);
-    if (VALS) val[r] = valid ? vin[idx] : 0u;
     unsigned d = valid ? (unsigned)((key[r] >> shift) & 0xFF) : 0x100u;
     unsigned peers = __match_any_sync(FULL, d);
     unsigned leader = (unsigned)(__ffs(peers) - 1);
@@ -197,7 +206,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
       wh[warp][d] = before + (uint32_t)__popc(peers);
     }
     before = __shfl_sync(FULL, before, leader);
-    lrank[r] = before + (uint32_t)__popc(peers & lanemask_lt());
+    const uint32_t lr = before + (uint32_t)__popc(peers & lanemask_lt());
+    if (r & 1) lrk[r >> 1] |= lr << 16;
+    else lrk[r >> 1] = lr;
     __syncwarp();
   }
   __syncthreads();
@@ -224,7 +235,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
     int64_t idx = base + r * 32 + lane;
     if (idx < N) {
       unsigned d = (unsigned)((key[r] >> shift) & 0xFF);
-      uint32_t pos = dstart[d] + wh[warp][d] + lrank[r];
+      const uint32_t lr = (r & 1) ? (lrk[r >> 1] >> 16) : (lrk[r >> 1] & 0xffffu);
+      uint32_t pos = dstart[d] + wh[warp][d] + lr;
       sk[pos] = key[r];
       if (VALS) sv[pos] = val[r];
     }
@@ -264,6 +276,7 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
   void* stmp = static_cast<char*>(tmp) + 2 * hist_bytes;
   size_t smem = sizeof(K) * RS_TILE + (VALS ? sizeof(uint32_t) * RS_TILE : 0);
   AOT_TRY(ensure_dyn_smem((const void*)k_radix_scatter<K, VALS>, smem));
+  AOT_TRY(prefer_max_smem((const void*)k_radix_scatter<K, VALS>));
   K* a = keys;
   K* b = keys_alt;
   uint32_t* va = vals;
