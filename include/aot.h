@@ -203,9 +203,12 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * tile by tile of the walked out-lists, a tile being the lists that fill
  * 2^tile_bits consecutive adjacency entries, so that the lists walked at the
  * same time stay in L2; 0 hands them out pivot by pivot.
+ * seg_tail (hub_mode 0): in every segment after the first, a long item with
+ * fewer than seg_tail entries left is walked by one thread instead of a warp
+ * (its later visits are short); 0 keeps every long item warp-wide.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
  * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
- * tile_bits 0.
+ * tile_bits 0, seg_tail 0.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
@@ -217,6 +220,7 @@ typedef struct {
   uint32_t seg_long;
   uint32_t seg_wide;
   uint32_t tile_bits;
+  uint32_t seg_tail;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

@@ -527,10 +527,16 @@ __device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, 
 
 // Takes the warp's next long item that has entries in the segment (nextv below
 // segHi) from the task's shared list; k = NONE when the list is done.
+// In a segment after the first, a long item with fewer than `tail` entries
+// left is walked by a thread instead (tail = 0: never).
+__device__ __forceinline__ bool tail_by_thread(uint32_t remaining, bool later_seg, uint32_t tail) {
+  return later_seg && remaining < tail;
+}
+
 __device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t nlong, uint32_t* next,
                                                const uint32_t* nextv, const uint32_t* cur,
-                                               const uint32_t* endp, uint32_t segHi, uint32_t& k,
-                                               uint32_t& x, uint32_t& y) {
+                                               const uint32_t* endp, uint32_t segHi, bool later_seg,
+                                               uint32_t tail, uint32_t& k, uint32_t& x, uint32_t& y) {
   const unsigned lane = lane_id();
   while (true) {
     uint32_t g = 0;
@@ -542,7 +548,8 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t n
       return;
     }
     k = longs[g];
-    if (nextv[k] < segHi) break;  // else nothing of this item in the segment
+    // else nothing of this item in the segment, or a thread walks it
+    if (nextv[k] < segHi && !tail_by_thread(endp[k] - cur[k], later_seg, tail)) break;
   }
   x = cur[k];
   y = endp[k];
@@ -696,6 +703,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
                                                                const uint32_t* __restrict__ ist,
                                                                uint32_t nh, uint32_t G, uint32_t seg_bits,
                                                                uint32_t seg_long, uint32_t seg_wide,
+                                                               uint32_t seg_tail,
                                                                const uint32_t* __restrict__ bofs,
                                                                const uint32_t* __restrict__ bnd,
                                                                uint64_t bcap) {
@@ -825,7 +833,8 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         if (MODE == M_TIMED && threadIdx.x == 0) s_stage += (unsigned long long)(clock64() - tset0) * (blockDim.x >> 5);
         // short items: a thread each
         for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
-          if (islong[k] || nextv[k] >= segHi) continue;
+          if ((islong[k] && !tail_by_thread(endp[k] - cur[k], sgm > 0, seg_tail)) || nextv[k] >= segHi)
+            continue;
           uint32_t x = cur[k], hk = ih[k], nv;
           uint32_t vj = 0;
           uint64_t tb = 0;
@@ -844,7 +853,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         const uint32_t nlong = s_nlong;
         while (true) {
           uint32_t k, x, y;
-          seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, k, x, y);
+          seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, sgm > 0, seg_tail, k, x, y);
           if (k == NONE) break;
           uint32_t hk = ih[k], nv;
           uint32_t vj = 0;
@@ -1042,7 +1051,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
-          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, bofs, bcap ? bnd : nullptr,
+          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, bofs,
+          bcap ? bnd : nullptr,
           bcap);
     AOT_TRY(last_launch());
   } else if (nh) {
@@ -1341,6 +1351,12 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
     for (uint32_t sb : segs) {
       aot_tuning t = cur;
       t.seg_bits = sb;
+      AOT_TRY(trial(t));
+    }
+    const uint32_t tails[] = {0u, 256u, 1024u, 4096u, 16384u};
+    for (uint32_t st : tails) {
+      aot_tuning t = cur;
+      t.seg_tail = st;
       AOT_TRY(trial(t));
     }
     const uint32_t tiles[] = {0u, 21u, 22u, 23u, 24u, 25u};

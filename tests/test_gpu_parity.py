@@ -126,6 +126,9 @@ def test_chunglu_full_parity():
     # every pivot on the bitmap path with 1024-rank segments: the per-pivot
     # segment bounds do not fit their scratch, so each segment end is searched
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024),
+    # later segments: long items with few entries left walked per thread
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=2048, seg_long=0, seg_tail=1 << 20),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024, seg_long=64, seg_tail=200),
     # walked-list tiles: none, several (clamped when most pivots are hubs)
     dict(tile_bits=0),
     dict(warp_max_outdeg=64, cta_max_outdeg=64, tile_bits=16),
@@ -136,13 +139,14 @@ def test_every_bin_gives_the_same_answer(tuning):
     check_full(n, s, d, tuning=tuning)
 
 
-@pytest.mark.parametrize("tile_bits,seg_bits", [(16, 1572864), (17, 4096), (0, 4096)])
-def test_walk_tiles(tile_bits, seg_bits):
+@pytest.mark.parametrize("tile_bits,seg_bits,seg_tail", [(16, 1572864, 0), (17, 4096, 0), (0, 4096, 0),
+                                                         (0, 4096, 512), (16, 8192, 1 << 30)])
+def test_walk_tiles(tile_bits, seg_bits, seg_tail):
     """Hub tasks handed out tile by tile of the walked out-lists (16 tiles of
     2^16 entries at R-MAT scale 16), with one or many bitmap segments."""
     n, s, d = gg.rmat_cfg(16, 5)
     check_full(n, s, d, tuning=dict(warp_max_outdeg=32, cta_max_outdeg=128, tile_bits=tile_bits,
-                                    seg_bits=seg_bits))
+                                    seg_bits=seg_bits, seg_tail=seg_tail))
 
 
 @pytest.mark.parametrize("case", ["rmat12", "er", "wheel", "k40", "chunglu"])
