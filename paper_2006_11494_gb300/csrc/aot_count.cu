@@ -363,9 +363,6 @@ __global__ void __launch_bounds__(256) k_hub_walk(KParams P, HubGroup G) {
 // thread each, longer ones by a warp in rounds of 128 entries (256 while at
 // least seg_wide entries remain).  Each pivot's segment bounds (positions in
 // N+(p)) are precomputed once per call by k_seg_bounds.
-#ifndef AOT_LONG_ORDER
-#define AOT_LONG_ORDER 0
-#endif
 constexpr int SEG_THREADS = 1024;
 constexpr uint32_t SEG_ITEMS = 1536;
 
@@ -783,9 +780,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       live |= r.x < r.y;
       const bool lg = r.y - r.x >= seg_long;  // long items are walked warp-wide
       islong[k] = lg;
-#if !AOT_LONG_ORDER
       if (lg) longs[atomicAdd(&s_nlong, 1u)] = k;
-#endif
     }
     if (!__syncthreads_or(live)) {  // nothing to walk: results only (zero hits)
       if (MODE == M_LIST_COUNT || MODE == M_TIMED)
@@ -799,19 +794,6 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     }
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
     uint32_t pc = pbeg;
-#if AOT_LONG_ORDER
-    if (wid == 0) {  // the long items in item order
-      uint32_t nl = 0;
-      for (uint32_t c = 0; c < nk; c += 32) {
-        const uint32_t k = c + lane;
-        const bool lg = k < nk && islong[k];
-        const unsigned bal = __ballot_sync(FULL, lg);
-        if (lg) longs[nl + (uint32_t)__popc(bal & lanemask_lt())] = k;
-        nl += (uint32_t)__popc(bal);
-      }
-      if (lane == 0) s_nlong = nl;
-    }
-#endif
     __syncthreads();
     uint32_t sgm = 0;
     for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += seg_bits, ++sgm) {
