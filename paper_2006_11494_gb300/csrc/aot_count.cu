@@ -1335,7 +1335,7 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       t.seg_bits = sb;
       AOT_TRY(trial(t));
     }
-    const uint32_t tails[] = {0u, 256u, 1024u, 4096u, 16384u};
+    const uint32_t tails[] = {0u, 128u, 192u, 256u, 384u, 512u};
     for (uint32_t st : tails) {
       aot_tuning t = cur;
       t.seg_tail = st;

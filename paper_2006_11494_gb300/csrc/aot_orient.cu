@@ -274,7 +274,8 @@ __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* _
                             int64_t m, int rule, const uint32_t* __restrict__ wofs,
                             const uint32_t* __restrict__ pscan, uint32_t* __restrict__ cursor,
                             uint2* __restrict__ witem, uint32_t* __restrict__ wvert,
-                            uint32_t* __restrict__ wedge) {
+                            uint32_t* __restrict__ wedge, uint64_t* __restrict__ walk,
+                            DevScalars* dev) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = e < m;
   uint32_t p = 0, x = 0;
@@ -302,29 +303,33 @@ __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* _
     wvert[slot] = x;
     wedge[slot] = (uint32_t)e;
   }
+  // walk length per pivot (one atomic per pivot present in the warp) and W
+  const uint32_t len = r.y - r.x;  // < 2^27 per item, < 2^32 for 32 items
+  const unsigned same = __match_any_sync(FULL, act ? p : 0xffffffffu);
+  const uint32_t gsum = __reduce_add_sync(same, len);
+  if (act && gsum && lane_id() == (unsigned)(__ffs(same) - 1))
+    atomicAdd((unsigned long long*)&walk[p], (unsigned long long)gsum);
+  const uint64_t wsum = warp_sum((uint64_t)len);
+  if (lane_id() == 0 && wsum) atomicAdd(&dev->total, (unsigned long long)wsum);
 }
 
-// warp per pivot: summed walk length; totals W and S
-__global__ void k_pivot_walk(const uint32_t* __restrict__ wofs, const uint2* __restrict__ witem,
-                             const uint32_t* __restrict__ outdeg, int32_t n,
-                             uint64_t* __restrict__ walk, DevScalars* dev) {
-  int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= n) return;
-  uint32_t b = wofs[p], e = wofs[p + 1];
-  uint64_t s = 0;
-  for (uint32_t i = b + lane_id(); i < e; i += 32) {
-    uint2 r = witem[i];
-    s += r.y - r.x;
-  }
-  s = warp_sum(s);
-  if (lane_id() == 0) {
-    walk[p] = s;
-    if (s) atomicAdd(&dev->total, (unsigned long long)s);
-    if (e > b) {
-      atomicAdd(&dev->aux[0], (unsigned long long)outdeg[p]);
-      // a merge of each item's walk with N+(p) reads deg+(p) more entries
-      atomicAdd(&dev->aux[1], (unsigned long long)(e - b) * outdeg[p]);
+// per pivot with items: S += deg+(p), merge work += items(p) deg+(p)
+__global__ void k_pivot_totals(const uint32_t* __restrict__ items, const uint32_t* __restrict__ outdeg,
+                               int32_t n, DevScalars* dev) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t st = 0, mw = 0;
+  if (p < n) {
+    const uint64_t it = items[p], d = outdeg[p];
+    if (it) {
+      st = d;
+      mw = it * d;  // a merge of each item's walk with N+(p) reads deg+(p) more entries
     }
+  }
+  st = warp_sum(st);
+  mw = warp_sum(mw);
+  if (lane_id() == 0) {
+    if (st) atomicAdd(&dev->aux[0], (unsigned long long)st);
+    if (mw) atomicAdd(&dev->aux[1], (unsigned long long)mw);
   }
 }
 
@@ -643,7 +648,8 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (n > 0) {
     if (cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
         cudaMemsetAsync(L.outdeg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
-        cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess)
+        cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
+        cudaMemsetAsync(L.walk, 0, sizeof(uint64_t) * n, s) != cudaSuccess)
       return fail(AOT_ERR_CUDA);
   }
   // 1. cleanup: keys, sort, unique
@@ -744,13 +750,13 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (m > 0) {
     AOT_KERNEL("k_item_fill", s)
       k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, item_rule(flags), L.wofs,
-                                             pscan, L.bin_flag, g->witem, g->wvert, g->wedge);
+                                             pscan, L.bin_flag, g->witem, g->wvert, g->wedge, L.walk,
+                                             L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   if (n > 0) {
-    AOT_KERNEL("k_pivot_walk", s)
-      k_pivot_walk<<<grid_for((int64_t)n * 32, T), T, 0, s>>>(L.wofs, g->witem, L.outdeg, n, L.walk,
-                                                           L.dev);
+    AOT_KERNEL("k_pivot_totals", s)
+      k_pivot_totals<<<grid_for(n, T), T, 0, s>>>(L.items, L.outdeg, n, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   DevScalars hs;
