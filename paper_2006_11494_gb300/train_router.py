@@ -100,7 +100,12 @@ def main():
         C.append(c)
         print("collected scale %d seed %d: %d items (%.1fs)" % (sc, seed, len(x), time.time() - t0), flush=True)
     X = np.concatenate(X).astype(np.float32)
-    Y = np.log1p(np.concatenate(C).astype(np.float64)).astype(np.float32)
+    Call = np.concatenate(C).astype(np.float64)
+    # upper bound of any per-item route on these items: every item in its
+    # cheapest variant, by its own recorded cycles
+    bound = float(Call[:, 0].sum() / Call.min(axis=1).sum())
+    print("perfect per-item routing on the sampled items: %.3fx the probe route" % bound, flush=True)
+    Y = np.log1p(Call).astype(np.float32)
     in_mean, in_std = X.mean(0), X.std(0) + 1e-3
     out_mean, out_std = Y.mean(0), Y.std(0) + 1e-3
     T = ((Y - out_mean) / out_std).astype(np.float32)
@@ -150,7 +155,8 @@ def main():
     meta = {"train_graphs": ["rmat s%d seed %d" % (scales[i % len(scales)], sd) for i, sd in enumerate(seeds[:-1])],
             "validation_graph": "rmat s%d seed %d" % (sc_val, seeds[-1]), "steps": steps,
             "batch": a.batch, "items": int(len(X)), "timings_ms": results,
-            "chosen_margin": best_margin, "speedup_on_validation": t_plain / best_ms}
+            "chosen_margin": best_margin, "speedup_on_validation": t_plain / best_ms,
+            "perfect_item_routing_bound": bound}
     router.save(a.out, params, im, isd, om, osd, best_margin, meta)
     print(json.dumps(meta), flush=True)
 
