@@ -297,8 +297,7 @@ __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* _
                             int64_t m, int rule, const uint32_t* __restrict__ wofs,
                             const uint32_t* __restrict__ pscan, uint32_t* __restrict__ cursor,
                             uint2* __restrict__ witem, uint32_t* __restrict__ wvert,
-                            uint32_t* __restrict__ wedge, uint64_t* __restrict__ walk,
-                            DevScalars* dev) {
+                            uint32_t* __restrict__ wedge) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = e < m;
   uint32_t p = 0, x = 0;
@@ -326,34 +325,73 @@ __global__ void k_item_fill(const uint32_t* __restrict__ esrc, const uint32_t* _
     wvert[slot] = x;
     wedge[slot] = (uint32_t)e;
   }
-  // walk length per pivot (one atomic per pivot present in the warp) and W
-  const uint32_t len = r.y - r.x;  // < 2^27 per item, < 2^32 for 32 items
-  const unsigned same = __match_any_sync(FULL, act ? p : 0xffffffffu);
-  const uint32_t gsum = __reduce_add_sync(same, len);
-  if (act && gsum && lane_id() == (unsigned)(__ffs(same) - 1))
-    atomicAdd((unsigned long long*)&walk[p], (unsigned long long)gsum);
-  const uint64_t wsum = warp_sum((uint64_t)len);
-  if (lane_id() == 0 && wsum) atomicAdd(&dev->total, (unsigned long long)wsum);
 }
 
-// per pivot with items: S += deg+(p), merge work += items(p) deg+(p)
-__global__ void k_pivot_totals(const uint32_t* __restrict__ items, const uint32_t* __restrict__ outdeg,
-                               int32_t n, DevScalars* dev) {
+// Per pivot: walk[p] = summed walk length of its items, and the totals W,
+// S += deg+(p) and merge work += items(p) deg+(p) (a merge of each item's
+// walk with N+(p) reads deg+(p) more entries).  A thread sums a pivot of at
+// most PW_SMALL items; larger pivots are listed for k_pivot_walk_big.
+constexpr uint32_t PW_SMALL = 64;
+__global__ void k_pivot_walk(const uint32_t* __restrict__ wofs, const uint2* __restrict__ witem,
+                             const uint32_t* __restrict__ outdeg, int32_t n, uint64_t* __restrict__ walk,
+                             uint32_t* __restrict__ big, DevScalars* dev) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t st = 0, mw = 0;
+  uint64_t w = 0, st = 0, mw = 0;
+  bool large = false;
   if (p < n) {
-    const uint64_t it = items[p], d = outdeg[p];
-    if (it) {
+    const uint32_t b = wofs[p], e = wofs[p + 1];
+    const uint64_t d = outdeg[p];
+    if (e > b) {
       st = d;
-      mw = it * d;  // a merge of each item's walk with N+(p) reads deg+(p) more entries
+      mw = (uint64_t)(e - b) * d;
+    }
+    large = e - b > PW_SMALL;
+    if (!large) {
+      for (uint32_t i = b; i < e; ++i) {
+        const uint2 r = witem[i];
+        w += r.y - r.x;
+      }
+      walk[p] = w;
     }
   }
+  const unsigned bal = __ballot_sync(FULL, large);
+  if (bal) {
+    const unsigned leader = (unsigned)(__ffs(bal) - 1);
+    uint32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(&dev->counters[13], (unsigned)__popc(bal));
+    base = __shfl_sync(FULL, base, leader);
+    if (large) big[base + (uint32_t)__popc(bal & lanemask_lt())] = (uint32_t)p;
+  }
+  w = warp_sum(w);
   st = warp_sum(st);
   mw = warp_sum(mw);
   if (lane_id() == 0) {
+    if (w) atomicAdd(&dev->total, (unsigned long long)w);
     if (st) atomicAdd(&dev->aux[0], (unsigned long long)st);
     if (mw) atomicAdd(&dev->aux[1], (unsigned long long)mw);
   }
+}
+
+// a warp per listed pivot (more than PW_SMALL items)
+__global__ void k_pivot_walk_big(const uint32_t* __restrict__ wofs, const uint2* __restrict__ witem,
+                                 const uint32_t* __restrict__ big, uint64_t* __restrict__ walk,
+                                 DevScalars* dev) {
+  const uint32_t nbig = dev->counters[13];
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  uint64_t tot = 0;
+  for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nbig; k += warps) {
+    const uint32_t p = big[k];
+    const uint32_t b = wofs[p], e = wofs[p + 1];
+    uint64_t w = 0;
+    for (uint32_t i = b + lane_id(); i < e; i += 32) {
+      const uint2 r = witem[i];
+      w += r.y - r.x;
+    }
+    w = warp_sum(w);
+    if (lane_id() == 0) walk[p] = w;
+    tot += w;
+  }
+  if (lane_id() == 0 && tot) atomicAdd(&dev->total, (unsigned long long)tot);
 }
 
 // --------------------------------------------------------------------- bins
@@ -671,8 +709,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (n > 0) {
     if (cudaMemsetAsync(L.deg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
         cudaMemsetAsync(L.outdeg, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
-        cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess ||
-        cudaMemsetAsync(L.walk, 0, sizeof(uint64_t) * n, s) != cudaSuccess)
+        cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess)
       return fail(AOT_ERR_CUDA);
   }
   // 1. cleanup: the hash set of the edge keys (the two key buffers, at least
@@ -763,13 +800,15 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   if (m > 0) {
     AOT_KERNEL("k_item_fill", s)
       k_item_fill<<<grid_for(m, T), T, 0, s>>>(esrc, L.adj, L.off, L.outdeg, m, item_rule(flags), L.wofs,
-                                             pscan, L.bin_flag, g->witem, g->wvert, g->wedge, L.walk,
-                                             L.dev);
+                                             pscan, L.bin_flag, g->witem, g->wvert, g->wedge);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
-  if (n > 0) {
-    AOT_KERNEL("k_pivot_totals", s)
-      k_pivot_totals<<<grid_for(n, T), T, 0, s>>>(L.items, L.outdeg, n, L.dev);
+  if (n > 0) {  // large-pivot list in bin_pos (n + 1 words, free until binning)
+    AOT_KERNEL("k_pivot_walk", s)
+      k_pivot_walk<<<grid_for(n, T), T, 0, s>>>(L.wofs, g->witem, L.outdeg, n, L.walk, L.bin_pos, L.dev);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    AOT_KERNEL("k_pivot_walk_big", s)
+      k_pivot_walk_big<<<(unsigned)(sm_count() * 8), T, 0, s>>>(L.wofs, g->witem, L.bin_pos, L.walk, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   DevScalars hs;
