@@ -2,10 +2,9 @@
 // out-CSR of Algorithm 3 (first step) and the per-pivot work items of its
 // adaptive orientation (Sec. 3.1-3.2).
 //
-//  cleanup   key = (min << b) | max per non-loop pair into a hash set; the
-//            first insertion of a key keeps it (the input is an undirected
-//            simple graph, Sec. 2.1)
-//  degree    deg(v) counted by those first insertions
+//  cleanup   key = (min << b) | max per non-loop pair, radix sort, unique
+//            (the input is an undirected simple graph, Sec. 2.1)
+//  degree    deg(v) over unique edges (warp-aggregated atomics)
 //  eta       stable radix sort of ids by degree (non-increasing by default),
 //            so ties keep the smaller id first (footnote of Sec. 3.2)
 //  orient    relabel to eta rank, key = (min rank << b) | max rank, radix
@@ -18,13 +17,30 @@
 
 namespace aot {
 
-// splitmix64's output function (Steele, Lea and Flood, "Fast splittable
-// pseudorandom number generators", OOPSLA 2014): spreads edge keys over the
-// hash table
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
+constexpr uint64_t INVALID_KEY = ~0ull;
+
+__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            int64_t E, int32_t n, int bits, uint64_t* __restrict__ keys,
+                            DevScalars* dev) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  int32_t a = src[i], b = dst[i];
+  uint64_t k = INVALID_KEY;
+  if (a < 0 || a >= n || b < 0 || b >= n) {
+    atomicOr(&dev->err, DEVERR_RANGE);
+  } else if (a != b) {
+    uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+    k = ((uint64_t)lo << bits) | hi;
+  }
+  keys[i] = k;
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t E,
+                               uint32_t* __restrict__ flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  uint64_t k = keys[i];
+  flags[i] = (k != INVALID_KEY && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
 }
 
 // warp-aggregated atomicAdd of 1 to cnt[key]
@@ -33,55 +49,16 @@ __device__ __forceinline__ void agg_inc(uint32_t* cnt, uint32_t key, bool active
   if (active && lane_id() == (unsigned)(__ffs(grp) - 1)) atomicAdd(&cnt[key], (uint32_t)__popc(grp));
 }
 
-// Cleanup (the input is an undirected simple graph, Sec. 2.1): every non-loop
-// pair becomes the key (min << bits) | max and is inserted into a hash set, an
-// open-addressing table of tsize >= 2E slots (load <= 1/2, linear probing,
-// empty = all ones, which no key equals).  The insertion that claims a slot
-// appends the key to ukeys and counts both endpoint degrees, so duplicates and
-// reversed pairs vanish.  ukeys comes out unordered; the orientation's sort
-// orders it.  Ids outside [0, n) raise the range error.
-__global__ void k_dedup(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t E,
-                        int32_t n, int bits, uint64_t* __restrict__ table, uint64_t tsize,
-                        uint64_t* __restrict__ ukeys, uint32_t* __restrict__ deg, DevScalars* dev) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool fresh = false;
-  uint64_t key = 0;
-  uint32_t lo = 0, hi = 0;
-  if (i < E) {
-    const int32_t a = src[i], b = dst[i];
-    if (a < 0 || a >= n || b < 0 || b >= n) {
-      atomicOr(&dev->err, DEVERR_RANGE);
-    } else if (a != b) {
-      lo = (uint32_t)min(a, b);
-      hi = (uint32_t)max(a, b);
-      key = ((uint64_t)lo << bits) | hi;
-      uint64_t slot = __umul64hi(mix64(key), tsize);
-      // at most tsize probes: the table is at most half full
-      for (uint64_t t = 0; t < tsize; ++t) {
-        const unsigned long long old =
-            atomicCAS(reinterpret_cast<unsigned long long*>(table + slot), ~0ull, (unsigned long long)key);
-        if (old == ~0ull) {
-          fresh = true;
-          break;
-        }
-        if (old == key) break;
-        if (++slot == tsize) slot = 0;
-        if (t + 1 == tsize) atomicOr(&dev->err, DEVERR_CHECK);
-      }
-    }
-  }
-  const unsigned bal = __ballot_sync(FULL, fresh);
-  if (bal) {
-    const unsigned leader = (unsigned)(__ffs(bal) - 1);
-    uint32_t base = 0;
-    if (lane_id() == leader) base = atomicAdd(&dev->counters[12], (unsigned)__popc(bal));
-    base = __shfl_sync(FULL, base, leader);
-    if (fresh) {
-      ukeys[base + (uint32_t)__popc(bal & lanemask_lt())] = key;
-      atomicAdd(&deg[lo], 1u);
-      atomicAdd(&deg[hi], 1u);
-    }
-  }
+__global__ void k_compact_unique(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ flags,
+                                 const uint32_t* __restrict__ pos, int64_t E, int bits,
+                                 uint64_t* __restrict__ ukeys, uint32_t* __restrict__ deg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = i < E && flags[i];
+  uint64_t k = act ? keys[i] : 0;
+  if (act) ukeys[pos[i]] = k;
+  uint32_t lo = (uint32_t)(k >> bits), hi = (uint32_t)(k & ((1ull << bits) - 1));
+  agg_inc(deg, lo, act);
+  agg_inc(deg, hi, act);
 }
 
 __global__ void k_eta_keys(const uint32_t* __restrict__ deg, int32_t n, int bits, bool desc,
@@ -712,29 +689,37 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
         cudaMemsetAsync(L.items, 0, sizeof(uint32_t) * n, s) != cudaSuccess)
       return fail(AOT_ERR_CUDA);
   }
-  // 1. cleanup: the hash set of the edge keys (the two key buffers, at least
-  // 2E slots), unique keys into the dead flags region (E + 1 words of 8 bytes)
+  // 1. cleanup: keys, sort, unique
   int64_t m = 0;
-  uint64_t* ukeys = reinterpret_cast<uint64_t*>(L.flags);
-  uint64_t* dead = L.keysA;
+  uint64_t* sorted = L.keysA;
+  uint64_t* other = L.keysB;
   if (E > 0) {
-    const uint64_t tsize = (uint64_t)((L.keysB + (E > 0 ? E : 1)) - L.keysA);
-    if (cudaMemsetAsync(L.keysA, 0xff, sizeof(uint64_t) * tsize, s)) return fail(AOT_ERR_CUDA);
-    AOT_KERNEL("k_dedup", s)
-      k_dedup<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, tsize, ukeys, L.deg, L.dev);
+    AOT_KERNEL("k_make_keys", s)
+      k_make_keys<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
+    aot_status st = radix_sort_u64(L.keysA, L.keysB, E, 2 * bits, L.tmp, s, &sorted);
+    if (st) return fail(st);
+    other = sorted == L.keysA ? L.keysB : L.keysA;
+    AOT_KERNEL("k_unique_flags", s)
+      k_unique_flags<<<grid_for(E, T), T, 0, s>>>(sorted, E, L.flags);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
+    st = scan_u32_u32(L.flags, L.pos, E, L.tmp, s);
+    if (st) return fail(st);
     uint32_t mm = 0;
-    if (cudaMemcpyAsync(&mm, &L.dev->counters[12], sizeof(uint32_t), cudaMemcpyDeviceToHost, s) ||
+    if (cudaMemcpyAsync(&mm, L.pos + E, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s))
       return fail(AOT_ERR_CUDA);
-    aot_status st = read_device_error(g, s);
+    st = read_device_error(g, s);
     if (st) return fail(st);
     m = mm;
+    AOT_KERNEL("k_compact_unique", s)
+      k_compact_unique<<<grid_for(E, T), T, 0, s>>>(sorted, L.flags, L.pos, E, bits, other, L.deg);
+    if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   g->m = m;
   // 2. eta: stable sort of ids by degree key (or by peeling round)
   if (n > 0 && (flags & AOT_ETA_DEGENERACY)) {
-    aot_status st = degeneracy_rounds(g, L, ukeys, dead, m, s);
+    aot_status st = degeneracy_rounds(g, L, other, sorted, m, s);
     if (st) return fail(st);
     AOT_KERNEL("k_iota", s)
       k_iota<<<grid_for(n, T), T, 0, s>>>(L.ev0, n);
@@ -754,13 +739,15 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     if (last_launch()) return fail(AOT_ERR_CUDA);
   }
   // 3. orient: relabel, sort, split into out-CSR
-  uint32_t* esrc = L.flags;  // the unique keys are dead once relabelled
+  uint32_t* esrc = L.flags;  // the cleanup flags are dead now
   if (m > 0) {
+    uint64_t* ukeys = other;
+    uint64_t* okeys = sorted;  // reuse the other buffer
     AOT_KERNEL("k_relabel", s)
-      k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, local_order(flags, bits), L.keysA);
+      k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, local_order(flags, bits), okeys);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     uint64_t* osorted;
-    aot_status st = radix_sort_u64(L.keysA, L.keysB, m, 2 * bits, L.tmp, s, &osorted);
+    aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, s, &osorted);
     if (st) return fail(st);
     AOT_KERNEL("k_split_csr", s)
       k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, local_order(flags, bits), L.adj, esrc,
