@@ -420,27 +420,21 @@ def run_ours(a):
     if not a.no_extras:
         extras["variants"] = variants(aot, src, dst, n, ws, stream, phase_ms, T)
 
-    # end to end: pinned host edge list in, per-vertex counts out, every step
+    # end to end: pinned host edge list in, per-vertex counts out, every step.
+    # Each step's input is copied on a copy stream into one of two device
+    # buffers while the previous step computes (a user's pipeline); the serial
+    # form (copy, then compute) is reported beside it.
     e2e = None
     if not a.no_e2e:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        d_src = torch.empty_like(src)
-        d_dst = torch.empty_like(dst)
-        torch.cuda.synchronize()
-        barrier()
-        e0.record(stream)
-        for _ in range(a.steps):
-            d_src.copy_(h_src, non_blocking=True)
-            d_dst.copy_(h_dst, non_blocking=True)
-            aot.aot_graph_destroy(step(d_src, d_dst))
-            h_counts.copy_(counts, non_blocking=True)
-            stream.synchronize()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+        e_ms, e_wall = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream,
+                                a.steps, True, barrier)
+        s_ms, _ = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream, a.steps,
+                           False, barrier)
+        e_ms = max_over_ranks(e_ms, dev)
         e2e = {"value": replica_value(info["m"], e_ms, world), "unit": UNIT, "ms_per_step": e_ms,
-               "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n}
-        del d_src, d_dst
+               "wall_ms_per_step": e_wall, "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n,
+               "copies": "overlapped with the previous step (two input buffers, a copy stream)",
+               "serial_ms_per_step": s_ms}
 
     if rank != 0:
         return
@@ -502,6 +496,48 @@ def run_ours(a):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream, steps, overlap, barrier):
+    """K steps from pinned host memory: copy the edge list in (copy stream),
+    orient + count, read the per-vertex counts back; with overlap, step i+1's
+    input is copied into the other buffer while step i computes.  Returns the
+    event time on the compute stream and the wall time per step (ms)."""
+    cs = torch.cuda.Stream(src.device)
+    bufs = [(torch.empty_like(src), torch.empty_like(dst)) for _ in range(2 if overlap else 1)]
+    ready = [torch.cuda.Event() for _ in bufs]
+    free = [torch.cuda.Event() for _ in bufs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def load(i):
+        b = i % len(bufs)
+        cs.wait_event(e0 if i < len(bufs) else free[b])
+        with torch.cuda.stream(cs):
+            bufs[b][0].copy_(h_src, non_blocking=True)
+            bufs[b][1].copy_(h_dst, non_blocking=True)
+        ready[b].record(cs)
+
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    if overlap:
+        load(0)
+    for i in range(steps):
+        b = i % len(bufs)
+        if not overlap:
+            load(i)
+        elif i + 1 < steps:
+            load(i + 1)
+        stream.wait_event(ready[b])
+        aot.aot_graph_destroy(step(*bufs[b]))
+        free[b].record(stream)
+        h_counts.copy_(counts, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3 / steps
+    return e0.elapsed_time(e1) / steps, wall
 
 
 # ------------------------------------------------------------ CPU oracle

@@ -161,3 +161,43 @@ def test_learned_route_is_invisible_in_the_output(aot, margin):
     T, t = g.count_per_vertex(aot.ROUTE_LEARNED)
     assert T == T_ref and np.array_equal(u64(t), t_ref)
     assert np.array_equal(g.list(aot.ROUTE_LEARNED, chunk=50000).cpu().numpy(), lst_ref)
+
+
+@pytest.mark.slow
+def test_learned_vs_plain_on_the_held_out_graph(aot):
+    """The committed router on the graph held out of its training (R-MAT s22,
+    seed 1019): the learned route at the committed margin and at margin 0 (the
+    network's own choice, which reroutes items) gives the plain route's exact
+    count and per-vertex counts; the measured speed-up is printed."""
+    import torch
+    from paper_2006_11494_gb300 import router
+    model = router.load()
+    assert model is not None
+    n, s, d = gg.rmat_cfg(22, 1019)
+    g = gpu_graph(n, s, d, aot.FLAG_NO_LIST)
+    T0, t0 = g.count_per_vertex()
+    t0 = u64(t0)
+
+    def timed(route):
+        best = 1e30
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            T = g.count(route)
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return T, best
+
+    T_plain, ms_plain = timed(aot.ROUTE_PLAIN)
+    for margin in (None, 0.0):
+        buf = model if margin is None else router.with_margin(model, margin)
+        aot.aot_graph_set_router(g.handle, buf)
+        T, ms = timed(aot.ROUTE_LEARNED)
+        Tv, tv = g.count_per_vertex(aot.ROUTE_LEARNED)
+        assert T == T_plain == Tv == T0
+        assert np.array_equal(u64(tv), t0)
+        print("held-out R-MAT s22: plain %.2f ms, learned (margin %s) %.2f ms, speed-up %.3f"
+              % (ms_plain, "committed" if margin is None else margin, ms, ms_plain / ms))
+    aot.aot_graph_set_router(g.handle, None)
