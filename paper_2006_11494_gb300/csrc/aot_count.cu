@@ -180,12 +180,28 @@ constexpr int WARP_TS = 128;  // slots per warp table of the warp bin (deg+ <= 6
 // come from queue q.  Used
 // for the warp bin and, with cta_threads = 32, for the CTA bin: no CTA-wide
 // barrier, so a pivot with long items holds up only its own warp.
+// words of a warp's shared memory: table, hit counters (per-vertex mode) and
+// the prefilter of 8 ts_max bits
+template <int MODE>
+__host__ __device__ constexpr size_t warp_pivot_words(uint32_t ts_max) {
+  return (size_t)(MODE == M_VERTEX ? 2 : 1) * ts_max + ts_max / 4;
+}
+
+// prefilter bit of w among 2^fbits: the high bits of a second multiplicative
+// hash (independent of the table slot, which takes the low bits)
+__device__ __forceinline__ uint32_t filter_bit(uint32_t w, int fbits) {
+  return (w * 0x85EBCA6Bu) >> (32 - fbits);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_warp_pivots(KParams P, uint32_t ts_max, int q) {
   extern __shared__ uint32_t wp_sm[];
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
-  uint32_t* tab = wp_sm + (size_t)wid * (MODE == M_VERTEX ? 2 : 1) * ts_max;
+  uint32_t* tab = wp_sm + (size_t)wid * warp_pivot_words<MODE>(ts_max);
   uint32_t* cnt = tab + ts_max;  // per-vertex mode only
+  // prefilter: 8 ts bits, one set for every entry of N+(p);
+  // a probe whose bit is clear misses without touching the table
+  uint32_t* filt = tab + (MODE == M_VERTEX ? 2 : 1) * ts_max;
   uint64_t found = 0;
   while (true) {
     uint32_t idx = 0;
@@ -197,21 +213,30 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P, uint32_t ts_max,
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
     const long long tst0 = MODE == M_TIMED ? clock64() : 0;
     uint32_t ts = 32;
-    while (ts < 2 * d) ts <<= 1;
+    int fbits = 8;  // log2 of the prefilter bits, 8 ts
+    while (ts < 2 * d) {
+      ts <<= 1;
+      ++fbits;
+    }
     const uint32_t mask = ts - 1;
     for (uint32_t i = lane; i < ts; i += 32) {
       tab[i] = EMPTY;
       if (MODE == M_VERTEX) cnt[i] = 0;
     }
+    for (uint32_t i = lane; i < ts / 4; i += 32) filt[i] = 0;
     __syncwarp();
     for (uint32_t i = lane; i < d; i += 32) {
       uint32_t w = P.adj[b + i], s = hash_slot(w, mask);
       while (atomicCAS(&tab[s], EMPTY, w) != EMPTY) s = (s + 1) & mask;
+      const uint32_t f = filter_bit(w, fbits);
+      atomicOr(&filt[f >> 5], 1u << (f & 31));
     }
     __syncwarp();
     const uint32_t stage_share = MODE == M_TIMED
         ? sat_cycles((clock64() - tst0) / (long long)max(1u, P.wofs[p + 1] - P.wofs[p])) : 0u;
     auto probe = [&](uint32_t w, uint32_t& slot) -> bool {
+      const uint32_t f = filter_bit(w, fbits);
+      if (!((filt[f >> 5] >> (f & 31)) & 1u)) return false;
       uint32_t s = hash_slot(w, mask);
       while (true) {
         uint32_t k = tab[s];
@@ -929,7 +954,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
   // a warp per pivot with ts_max-slot tables; warps per CTA chosen (8, 4, 2
   // or 1) for the most resident warps
   auto launch_warps = [&](uint32_t count, uint32_t ts_max, int q, const char* name) -> aot_status {
-    const size_t per_warp = (size_t)(MODE == M_VERTEX ? 2 : 1) * ts_max * sizeof(uint32_t);
+    const size_t per_warp = warp_pivot_words<MODE>(ts_max) * sizeof(uint32_t);
     const size_t smem_cap = 227 * 1024;
     const size_t attr = per_warp * 8 < smem_cap ? per_warp * 8 : smem_cap;
     AOT_TRY(ensure_dyn_smem((const void*)k_warp_pivots<MODE>, attr));
