@@ -206,9 +206,12 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * seg_tail (hub_mode 0): in every segment after the first, a long item with
  * fewer than seg_tail entries left is walked by one thread instead of a warp
  * (its later visits are short); 0 keeps every long item warp-wide.
+ * seg_threads (hub_mode 0): threads per CTA of the segmented bitmap kernel, a
+ * multiple of 32 in [256, 1024]; with 512 and seg_bits <= 589824 two CTAs fit
+ * one SM.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
  * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
- * tile_bits 0, seg_tail 256.
+ * tile_bits 0, seg_tail 256, seg_threads 1024.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
@@ -221,6 +224,7 @@ typedef struct {
   uint32_t seg_wide;
   uint32_t tile_bits;
   uint32_t seg_tail;
+  int32_t seg_threads;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

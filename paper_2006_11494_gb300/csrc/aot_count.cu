@@ -1055,9 +1055,10 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     P.pivots = dp;
     P.num_pivots = nh;
     int per_sm = 0;
-    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, SEG_THREADS, seg_smem));
+    const int seg_threads = g->tune.seg_threads;
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, seg_threads, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
-      k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), SEG_THREADS, seg_smem, s>>>(
+      k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), seg_threads, seg_smem, s>>>(
           P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, bofs,
           bcap ? bnd : nullptr,
           bcap);
@@ -1359,6 +1360,15 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       aot_tuning t = cur;
       t.seg_bits = sb;
       AOT_TRY(trial(t));
+    }
+    {  // two CTAs of 512 threads per SM need segments of at most 576 K ranks
+      const uint32_t segs2[] = {524288u, 589824u};
+      for (uint32_t sb : segs2) {
+        aot_tuning t = cur;
+        t.seg_threads = 512;
+        t.seg_bits = sb;
+        AOT_TRY(trial(t));
+      }
     }
     const uint32_t tails[] = {0u, 128u, 192u, 256u, 384u, 512u};
     for (uint32_t st : tails) {
