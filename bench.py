@@ -254,19 +254,19 @@ def pinned_host(count, np_dtype, torch):
 
 # ------------------------------------------------------- algorithmic bytes
 def bytes_per_kernel(info, bins, E, n):
-    """Algorithmic HBM bytes of one step, per kernel family: each radix pass
-    reads (histogram) and moves (scatter) every key once; an intersection bin
+    """Algorithmic HBM bytes of one step, per kernel family: the radix sort
+    reads every key once for its histograms and moves every key (and value)
+    once per pass; an intersection bin
     stages N+(p) of its pivots, reads their offsets and their items' walk
     ranges and walked vertices, and every walked adjacency entry once."""
     m, bits = info["m"], max(1, math.ceil(math.log2(max(n, 2))))
     passes_keys = math.ceil(2 * bits / 8)
     passes_eta = math.ceil(bits / 8)
     out = {}
-    # radix sort: scatter reads and writes every key (and value) once per pass
-    out["k_radix_scatter"] = (passes_keys * (16 * E + 16 * m) + passes_eta * 16 * n,
-                              2 * passes_keys + passes_eta)
-    out["k_radix_hist"] = (passes_keys * (8 * E + 8 * m) + passes_eta * 4 * n,
-                           2 * passes_keys + passes_eta)
+    # radix sort: each sweep reads and writes every key (and value) once
+    out["k_onesweep"] = (passes_keys * (16 * E + 16 * m) + passes_eta * 16 * n,
+                         2 * passes_keys + passes_eta)
+    out["k_digit_hist"] = (8 * E + 8 * m + 4 * n, 3)
 
     def walk_bytes(b):
         st = bins[b]

@@ -113,11 +113,12 @@ aot_status scan_u64_u64(const uint64_t* in, uint64_t* out, int64_t N, void* tmp,
 
 // LSD radix sort on bits [0, bits) of the keys; stable.  Returns (via *out)
 // whichever of the two key buffers holds the result (and the values with it).
+// A bounded wait that runs out sets DEVERR_TIMEOUT in *err (a device word).
 size_t radix_tmp_bytes(int64_t N);
 aot_status radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, int64_t N, int bits, void* tmp,
-                          cudaStream_t s, uint64_t** out);
+                          uint32_t* err, cudaStream_t s, uint64_t** out);
 aot_status radix_sort_u32_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                                uint32_t* vals_alt, int64_t N, int bits, void* tmp,
+                                uint32_t* vals_alt, int64_t N, int bits, void* tmp, uint32_t* err,
                                 cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out);
 
 // ------------------------------------------------------------ graph handle

@@ -697,7 +697,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
     AOT_KERNEL("k_make_keys", s)
       k_make_keys<<<grid_for(E, T), T, 0, s>>>(d_src, d_dst, E, n, bits, L.keysA, L.dev);
     if (last_launch()) return fail(AOT_ERR_CUDA);
-    aot_status st = radix_sort_u64(L.keysA, L.keysB, E, 2 * bits, L.tmp, s, &sorted);
+    aot_status st = radix_sort_u64(L.keysA, L.keysB, E, 2 * bits, L.tmp, &L.dev->err, s, &sorted);
     if (st) return fail(st);
     other = sorted == L.keysA ? L.keysB : L.keysA;
     AOT_KERNEL("k_unique_flags", s)
@@ -732,7 +732,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
   }
   if (n > 0) {
     uint32_t *ko, *vo;
-    aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, s, &ko, &vo);
+    aot_status st = radix_sort_u32_pairs(L.ek0, L.ek1, L.ev0, L.ev1, n, bits, L.tmp, &L.dev->err, s, &ko, &vo);
     if (st) return fail(st);
     AOT_KERNEL("k_rank_from_perm", s)
       k_rank_from_perm<<<grid_for(n, T), T, 0, s>>>(vo, n, L.deg, L.perm, L.rank, L.degr);
@@ -747,7 +747,7 @@ extern "C" aot_status aot_orient(const int32_t* d_src, const int32_t* d_dst, int
       k_relabel<<<grid_for(m, T), T, 0, s>>>(ukeys, m, bits, L.rank, local_order(flags, bits), okeys);
     if (last_launch()) return fail(AOT_ERR_CUDA);
     uint64_t* osorted;
-    aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, s, &osorted);
+    aot_status st = radix_sort_u64(okeys, ukeys, m, 2 * bits, L.tmp, &L.dev->err, s, &osorted);
     if (st) return fail(st);
     AOT_KERNEL("k_split_csr", s)
       k_split_csr<<<grid_for(m, T), T, 0, s>>>(osorted, m, bits, local_order(flags, bits), L.adj, esrc,

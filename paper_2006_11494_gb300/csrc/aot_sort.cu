@@ -2,10 +2,10 @@
 //
 // Scan: three phases per level (tile reduce, recursive scan of the tile sums,
 // tile scan with offsets); tile = 256 threads x 8 items.
-// Radix sort: 8-bit digits, per pass (1) per-tile digit histograms, (2) an
-// exclusive scan of the digit-major histogram table, (3) a stable scatter
-// that ranks keys inside each warp with __match_any_sync, stages the tile in
-// shared memory in digit order and writes each digit run contiguously.
+// Radix sort: 8-bit digits; one histogram pass over all digits, then one
+// sweep per digit with decoupled look-back for the tiles' output offsets
+// (each wait bounded), ranking keys inside each warp with __match_any_sync
+// and writing each digit run of a tile contiguously.
 #include "aot_internal.cuh"
 
 namespace aot {
@@ -129,45 +129,84 @@ aot_status scan_u64_u64(const uint64_t* in, uint64_t* out, int64_t N, void* tmp,
 }
 
 // ---------------------------------------------------------------- radix sort
+// LSD radix sort with 8-bit digits, one sweep per digit.  A first kernel
+// counts every digit of every key (all passes at once) into global
+// histograms, whose exclusive scans give each digit's first output position.
+// Per pass, a CTA takes the next tile of 4096 keys from a counter (so every
+// earlier tile is already held by a running or finished CTA), ranks its keys
+// inside each warp with __match_any_sync, publishes its per-digit counts, and
+// adds up the counts of the earlier tiles by looking back over what they
+// published (decoupled look-back: a tile that has finished its look-back
+// publishes its inclusive prefix, which ends the look-back of later tiles).
+// Every wait on an unpublished predecessor is bounded: when it runs out the
+// kernel sets the timeout bit of the error word and goes on.  The tile is
+// staged in shared memory in digit order and written in contiguous runs.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 16;                       // keys per lane
 constexpr int RS_WARP_KEYS = 32 * RS_ROUNDS;        // 512
 constexpr int RS_TILE = RS_WARPS * RS_WARP_KEYS;    // 4096
 constexpr int RS_BUCKETS = 256;
+constexpr int RS_MAX_PASSES = 8;                    // 64-bit keys
 
+// look-back status words: flag in the top two bits, count below
+constexpr uint64_t LB_AGG = 1ull << 62;             // the tile's own counts
+constexpr uint64_t LB_PREFIX = 2ull << 62;          // the tile's and every earlier tile's
+constexpr uint64_t LB_VALUE = (1ull << 62) - 1;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;        // polls of one predecessor (~seconds)
+
+// Global histograms of every digit (passes x 256), per-warp copies in shared
+// memory (no lane serialisation across warps), grid-stride over the keys.
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int64_t N,
-                                                           int shift, uint32_t* __restrict__ hist,
-                                                           int64_t tiles) {
-  __shared__ uint32_t h[RS_BUCKETS];
-  h[threadIdx.x] = 0;
-  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  int64_t base = (int64_t)blockIdx.x * RS_TILE + warp * RS_WARP_KEYS;
-  unsigned dig[RS_ROUNDS];  // every load of the lane in flight before the first ranking
-#pragma unroll
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    int64_t idx = base + r * 32 + lane;
-    dig[r] = idx < N ? (unsigned)((__ldcs(keys + idx) >> shift) & 0xFF) : 0x100u;
+__global__ void __launch_bounds__(RS_THREADS) k_digit_hist(const K* __restrict__ keys, int64_t N,
+                                                           int passes, uint32_t* __restrict__ hist) {
+  extern __shared__ uint32_t dh[];  // [RS_WARPS][passes][256]
+  const unsigned warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < RS_WARPS * passes * RS_BUCKETS; i += RS_THREADS) dh[i] = 0;
+  __syncthreads();
+  uint32_t* mine = dh + (size_t)warp * passes * RS_BUCKETS;
+  const int64_t stride = (int64_t)gridDim.x * RS_THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < N; i += stride) {
+    const K k = __ldcs(keys + i);
+    for (int p = 0; p < passes; ++p) atomicAdd(&mine[p * RS_BUCKETS + (unsigned)((k >> (8 * p)) & 0xFF)], 1u);
   }
   __syncthreads();
-#pragma unroll
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    const unsigned d = dig[r];
-    unsigned peers = __match_any_sync(FULL, d);
-    if (d < 0x100u && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  for (int i = threadIdx.x; i < passes * RS_BUCKETS; i += RS_THREADS) {
+    uint32_t c = 0;
+    for (int w = 0; w < RS_WARPS; ++w) c += dh[w * passes * RS_BUCKETS + i];
+    if (c) atomicAdd(&hist[i], c);
   }
+}
+
+// exclusive scan of each pass's 256 digit counts: the digit's first position
+__global__ void __launch_bounds__(RS_THREADS) k_digit_base(const uint32_t* __restrict__ hist,
+                                                           uint32_t* __restrict__ base) {
+  __shared__ uint32_t wtot[RS_WARPS];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, t = threadIdx.x;
+  const uint32_t c = hist[blockIdx.x * RS_BUCKETS + t];
+  const uint32_t incl = warp_inclusive_scan(c);
+  if (lane == 31) wtot[warp] = incl;
   __syncthreads();
-  hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+  uint32_t wp = 0;
+  for (int w = 0; w < (int)warp; ++w) wp += wtot[w];
+  base[blockIdx.x * RS_BUCKETS + t] = wp + incl - c;
+}
+
+__device__ __forceinline__ uint64_t lb_load(const uint64_t* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void lb_store(uint64_t* p, uint64_t v) {
+  atomicExch(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
 template <class K, bool VALS>
-__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __restrict__ kin,
-                                                              const uint32_t* __restrict__ vin,
-                                                              int64_t N, int shift,
-                                                              const uint32_t* __restrict__ offs,
-                                                              int64_t tiles, K* __restrict__ kout,
-                                                              uint32_t* __restrict__ vout) {
+__global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin, int64_t N,
+                                                         int shift, const uint32_t* __restrict__ dbase,
+                                                         uint64_t* __restrict__ status,
+                                                         unsigned int* __restrict__ tile_ctr,
+                                                         K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         uint32_t* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char rs_smem[];
   K* sk = reinterpret_cast<K*>(rs_smem);
   uint32_t* sv = reinterpret_cast<uint32_t*>(rs_smem + sizeof(K) * RS_TILE);
@@ -175,13 +214,14 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __rest
   __shared__ uint32_t dstart[RS_BUCKETS];
   __shared__ uint32_t gofs[RS_BUCKETS];
   __shared__ uint32_t wtot[RS_WARPS];
+  __shared__ uint32_t s_tile;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5, t = threadIdx.x;
 #pragma unroll
   for (int w = 0; w < RS_WARPS; ++w) wh[w][t] = 0;
-  gofs[t] = offs[(int64_t)t * tiles + blockIdx.x];
+  if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
-
-  const int64_t tile_base = (int64_t)blockIdx.x * RS_TILE;
+  const uint32_t tile = s_tile;
+  const int64_t tile_base = (int64_t)tile * RS_TILE;
   const int64_t base = tile_base + warp * RS_WARP_KEYS;
   K key[RS_ROUNDS];
   uint32_t val[RS_ROUNDS];
@@ -212,7 +252,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __rest
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, digit totals
+  // per digit t: exclusive prefix over warps and the tile's count
   uint32_t tot = 0;
 #pragma unroll
   for (int w = 0; w < RS_WARPS; ++w) {
@@ -220,7 +260,33 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __rest
     wh[w][t] = tot;
     tot += c;
   }
-  // block exclusive scan of the 256 digit totals
+  // publish this tile's count of digit t, then add up the earlier tiles'
+  uint64_t* st = status + (size_t)tile * RS_BUCKETS + t;
+  uint64_t excl = 0;
+  if (tile == 0) {
+    lb_store(st, LB_PREFIX | tot);
+  } else {
+    lb_store(st, LB_AGG | tot);
+    int64_t pt = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (true) {
+      const uint64_t v = lb_load(status + (size_t)pt * RS_BUCKETS + t);
+      if (!(v & ~LB_VALUE)) {  // not published yet
+        if (++spins >= LB_SPIN_LIMIT) {
+          atomicOr(err, DEVERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      excl += v & LB_VALUE;
+      if ((v & ~LB_VALUE) == LB_PREFIX || pt == 0) break;
+      --pt;
+    }
+    lb_store(st, LB_PREFIX | (excl + tot));
+  }
+  gofs[t] = dbase[t] + (uint32_t)excl;
+  // block exclusive scan of the 256 digit totals: digit runs inside the tile
   uint32_t incl = warp_inclusive_scan(tot);
   if (lane == 31) wtot[warp] = incl;
   __syncthreads();
@@ -253,42 +319,57 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(const K* __rest
   }
 }
 
+// tmp: histograms and digit bases (passes x 256 each), tile counters, and the
+// look-back status words (tiles x 256)
 size_t radix_tmp_bytes(int64_t N) {
   int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
   if (tiles < 1) tiles = 1;
-  size_t hist = ((size_t)RS_BUCKETS * tiles + 1) * sizeof(uint32_t);
-  hist = (hist + 255) & ~size_t(255);
-  return 2 * hist + scan_tmp_bytes((int64_t)RS_BUCKETS * tiles) + 256;
+  return 2 * (size_t)RS_MAX_PASSES * RS_BUCKETS * sizeof(uint32_t) + 256 +
+         (size_t)tiles * RS_BUCKETS * sizeof(uint64_t) + 256;
 }
 
 template <class K, bool VALS>
 static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t N,
-                             int bits, void* tmp, cudaStream_t s, K** kout, uint32_t** vout) {
+                             int bits, void* tmp, uint32_t* err, cudaStream_t s, K** kout,
+                             uint32_t** vout) {
   *kout = keys;
   if (vout) *vout = vals;
   if (N <= 1 || bits <= 0) return AOT_OK;
-  // the combined table index (digit * tiles + tile) must fit uint32
+  // output positions are 32-bit
   if ((uint64_t)N + RS_TILE > 0xF0000000ull) return AOT_ERR_OVERFLOW;
-  int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
-  size_t hist_bytes = (((size_t)RS_BUCKETS * tiles + 1) * sizeof(uint32_t) + 255) & ~size_t(255);
-  uint32_t* hist = static_cast<uint32_t*>(tmp);
-  uint32_t* offs = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + hist_bytes);
-  void* stmp = static_cast<char*>(tmp) + 2 * hist_bytes;
-  size_t smem = sizeof(K) * RS_TILE + (VALS ? sizeof(uint32_t) * RS_TILE : 0);
-  AOT_TRY(ensure_dyn_smem((const void*)k_radix_scatter<K, VALS>, smem));
-  AOT_TRY(prefer_max_smem((const void*)k_radix_scatter<K, VALS>));
+  const int passes = (bits + 7) / 8;
+  if (passes > (int)sizeof(K)) return AOT_ERR_INVALID_ARG;
+  const int64_t tiles = (N + RS_TILE - 1) / RS_TILE;
+  char* c = static_cast<char*>(tmp);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(c);
+  uint32_t* dbase = hist + RS_MAX_PASSES * RS_BUCKETS;
+  unsigned int* ctr = reinterpret_cast<unsigned int*>(dbase + RS_MAX_PASSES * RS_BUCKETS);
+  uint64_t* status = reinterpret_cast<uint64_t*>(c + 2 * (size_t)RS_MAX_PASSES * RS_BUCKETS * sizeof(uint32_t) + 256);
+  const size_t status_bytes = (size_t)tiles * RS_BUCKETS * sizeof(uint64_t);
+  AOT_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * RS_MAX_PASSES * RS_BUCKETS, s));
+  AOT_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * RS_MAX_PASSES, s));
+  const size_t hsmem = (size_t)RS_WARPS * passes * RS_BUCKETS * sizeof(uint32_t);
+  AOT_TRY(ensure_dyn_smem((const void*)k_digit_hist<K>, hsmem));
+  int64_t hgrid = (int64_t)sm_count() * 8;
+  if (hgrid > tiles) hgrid = tiles;
+  AOT_KERNEL("k_digit_hist", s)
+    k_digit_hist<K><<<(unsigned)hgrid, RS_THREADS, hsmem, s>>>(keys, N, passes, hist);
+  AOT_TRY(last_launch());
+  AOT_KERNEL("k_digit_base", s)
+    k_digit_base<<<(unsigned)passes, RS_THREADS, 0, s>>>(hist, dbase);
+  AOT_TRY(last_launch());
+  const size_t smem = sizeof(K) * RS_TILE + (VALS ? sizeof(uint32_t) * RS_TILE : 0);
+  AOT_TRY(ensure_dyn_smem((const void*)k_onesweep<K, VALS>, smem));
+  AOT_TRY(prefer_max_smem((const void*)k_onesweep<K, VALS>));
   K* a = keys;
   K* b = keys_alt;
   uint32_t* va = vals;
   uint32_t* vb = vals_alt;
-  for (int shift = 0; shift < bits; shift += 8) {
-    AOT_KERNEL("k_radix_hist", s)
-      k_radix_hist<K><<<(unsigned)tiles, RS_THREADS, 0, s>>>(a, N, shift, hist, tiles);
-    AOT_TRY(last_launch());
-    AOT_TRY(scan_u32_u32(hist, offs, (int64_t)RS_BUCKETS * tiles, stmp, s));
-    AOT_KERNEL("k_radix_scatter", s)
-      k_radix_scatter<K, VALS><<<(unsigned)tiles, RS_THREADS, smem, s>>>(a, va, N, shift, offs,
-                                                                         tiles, b, vb);
+  for (int p = 0; p < passes; ++p) {
+    AOT_CUDA(cudaMemsetAsync(status, 0, status_bytes, s));
+    AOT_KERNEL("k_onesweep", s)
+      k_onesweep<K, VALS><<<(unsigned)tiles, RS_THREADS, smem, s>>>(a, va, N, 8 * p, dbase + p * RS_BUCKETS,
+                                                                    status, ctr + p, b, vb, err);
     AOT_TRY(last_launch());
     K* t = a; a = b; b = t;
     uint32_t* tv = va; va = vb; vb = tv;
@@ -299,15 +380,15 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
 }
 
 aot_status radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, int64_t N, int bits, void* tmp,
-                          cudaStream_t s, uint64_t** out) {
-  return radix_impl<uint64_t, false>(keys, keys_alt, nullptr, nullptr, N, bits, tmp, s, out,
+                          uint32_t* err, cudaStream_t s, uint64_t** out) {
+  return radix_impl<uint64_t, false>(keys, keys_alt, nullptr, nullptr, N, bits, tmp, err, s, out,
                                      nullptr);
 }
 
 aot_status radix_sort_u32_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
-                                uint32_t* vals_alt, int64_t N, int bits, void* tmp,
+                                uint32_t* vals_alt, int64_t N, int bits, void* tmp, uint32_t* err,
                                 cudaStream_t s, uint32_t** keys_out, uint32_t** vals_out) {
-  return radix_impl<uint32_t, true>(keys, keys_alt, vals, vals_alt, N, bits, tmp, s, keys_out,
+  return radix_impl<uint32_t, true>(keys, keys_alt, vals, vals_alt, N, bits, tmp, err, s, keys_out,
                                     vals_out);
 }
 
