@@ -211,7 +211,7 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * one SM.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
  * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
- * tile_bits 0, seg_tail 256, seg_threads 1024.
+ * tile_bits 0, seg_tail 128, seg_threads 1024.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;

@@ -1355,12 +1355,17 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       t.seg_wide = sw;
       AOT_TRY(trial(t));
     }
+    // segment width and the later segments' per-thread threshold interact:
+    // search them jointly
     const uint32_t segs[] = {1572864u, 1048576u};
-    for (uint32_t sb : segs) {
-      aot_tuning t = cur;
-      t.seg_bits = sb;
-      AOT_TRY(trial(t));
-    }
+    const uint32_t tails[] = {64u, 96u, 128u, 160u, 192u, 256u};
+    for (uint32_t sb : segs)
+      for (uint32_t st : tails) {
+        aot_tuning t = cur;
+        t.seg_bits = sb;
+        t.seg_tail = st;
+        AOT_TRY(trial(t));
+      }
     {  // two CTAs of 512 threads per SM need segments of at most 576 K ranks
       const uint32_t segs2[] = {524288u, 589824u};
       for (uint32_t sb : segs2) {
@@ -1369,12 +1374,6 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
         t.seg_bits = sb;
         AOT_TRY(trial(t));
       }
-    }
-    const uint32_t tails[] = {0u, 128u, 192u, 256u, 384u, 512u};
-    for (uint32_t st : tails) {
-      aot_tuning t = cur;
-      t.seg_tail = st;
-      AOT_TRY(trial(t));
     }
     const uint32_t tiles[] = {0u, 21u, 22u, 23u, 24u, 25u};
     for (uint32_t tb : tiles) {

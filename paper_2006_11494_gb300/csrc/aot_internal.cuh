@@ -136,7 +136,7 @@ struct Tuning {
   uint32_t seg_wide = 512;            // hub_mode 0: warp walks take rounds of 256 while this many entries remain
   uint32_t seg_long = 128;            // hub_mode 0: items this long walked warp-wide, shorter ones per thread
   uint32_t tile_bits = 0;             // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
-  uint32_t seg_tail = 256;            // hub_mode 0: after the first segment, items with fewer entries left walk per thread
+  uint32_t seg_tail = 128;            // hub_mode 0: after the first segment, items with fewer entries left walk per thread
   int seg_threads = 1024;             // hub_mode 0: threads per CTA of the segmented bitmap kernel
 };
 
