@@ -209,13 +209,9 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * seg_threads (hub_mode 0): threads per CTA of the segmented bitmap kernel, a
  * multiple of 32 in [256, 1024]; with 512 and seg_bits <= 589824 two CTAs fit
  * one SM.
- * vx_agg (hub_mode 0, per-vertex counting): 0, or a power of two in
- * [1024, 16384]: slots of a shared-memory table that gathers the third
- * vertex's counts of a task before one global update per vertex; used only
- * when it fits beside the bitmap (seg_bits of about 1 M ranks or less).
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
  * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
- * tile_bits 0, seg_tail 128, seg_threads 1024, vx_agg 0.
+ * tile_bits 0, seg_tail 128, seg_threads 1024.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
@@ -229,7 +225,6 @@ typedef struct {
   uint32_t tile_bits;
   uint32_t seg_tail;
   int32_t seg_threads;
-  uint32_t vx_agg;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

@@ -89,8 +89,7 @@ class Tuning(ctypes.Structure):
                 ("hub_mode", ctypes.c_int32), ("seg_bits", ctypes.c_uint32),
                 ("seg_long", ctypes.c_uint32),
                 ("seg_wide", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32),
-                ("seg_tail", ctypes.c_uint32), ("seg_threads", ctypes.c_int32),
-                ("vx_agg", ctypes.c_uint32)]
+                ("seg_tail", ctypes.c_uint32), ("seg_threads", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

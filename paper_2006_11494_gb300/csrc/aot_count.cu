@@ -442,10 +442,6 @@ __device__ __forceinline__ uint32_t warp_partition(uint32_t lo, uint32_t hi, Les
 }
 
 constexpr uint32_t SEG_MAXB = 512;  // segment bounds of one pivot held in shared memory
-// static shared memory of k_seg_pivots (segment bounds and scalars), and the
-// per-block limit of dynamic + static shared memory
-constexpr size_t SEG_STATIC_SMEM = SEG_MAXB * 4 + 64;
-constexpr size_t SMEM_PER_BLOCK_MAX = 227 * 1024;
 
 // Work groups of the hub pivots, a warp per pivot.  A pivot's positive items
 // come first, sorted by their walked vertex v (larger rank than the pivot),
@@ -528,50 +524,18 @@ __global__ void k_seg_bounds(const uint32_t* __restrict__ pivots, uint32_t nh,
 }
 
 
-// Third-vertex counts of one task gathered in shared memory (per-vertex mode):
-// an open-addressing table w -> hits over the task's pivot's out-neighbours,
-// flushed to t(w) when the task ends, so that a vertex hit by many items of
-// the task costs one global atomic instead of one per hit.  A hit that finds
-// no slot within four probes goes to t(w) directly.  key == nullptr: no table.
-struct VxAgg {
-  uint32_t* key;
-  uint32_t* cnt;
-  uint32_t mask;
-  int shift;  // 32 - log2(slots)
-};
-
-__device__ __forceinline__ void vx_hit(const KParams& P, const VxAgg& A, uint32_t w) {
-  if (A.key) {
-    uint32_t s = (w * 2654435761u) >> A.shift;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      uint32_t k = A.key[s];
-      if (k == EMPTY) {
-        k = atomicCAS(&A.key[s], EMPTY, w);
-        if (k == EMPTY) k = w;
-      }
-      if (k == w) {
-        atomicAdd(&A.cnt[s], 1u);
-        return;
-      }
-      s = (s + 1) & A.mask;
-    }
-  }
-  atomicAdd((unsigned long long*)&P.tv[w], 1ull);
-}
-
 // Hits of one round: per-lane count, and in per-vertex and listing modes the
 // third vertices (listing ranks follow the warp's lane order).
 template <int MODE, int E>
-__device__ __forceinline__ void seg_count_hits(const KParams& P, const VxAgg& A, unsigned hits,
-                                               const uint32_t (&e)[E], uint32_t& lane_hits, uint32_t& hk,
-                                               uint32_t p, uint32_t vj, uint64_t tb) {
+__device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t (&e)[E],
+                                               uint32_t& lane_hits, uint32_t& hk, uint32_t p,
+                                               uint32_t vj, uint64_t tb) {
   const uint32_t c = (uint32_t)__popc(hits);
   lane_hits += c;
   if (MODE == M_VERTEX) {
 #pragma unroll
     for (int j = 0; j < E; ++j)
-      if (hits & (1u << j)) vx_hit(P, A, e[j]);
+      if (hits & (1u << j)) atomicAdd((unsigned long long*)&P.tv[e[j]], 1ull);
   }
   if (MODE == M_LIST_WRITE) {
     const uint32_t incl = warp_inclusive_scan(c);
@@ -629,7 +593,7 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t n
 // never reads past the allocation.
 // x: cursor (updated), hk: hits of the item so far (updated).
 template <int MODE, int E>
-__device__ __forceinline__ void seg_walk_item(const KParams& P, const VxAgg& A, const uint32_t* bm, uint32_t seg_words,
+__device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t seg_words,
                                               uint32_t segLo, uint32_t segHi, uint32_t& x, uint32_t y,
                                               uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
@@ -690,7 +654,7 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const VxAgg& A, 
       const uint32_t val = __shfl_sync(FULL, at, (rel / E) & 31u);
       next_val = stop < y ? val : NONE;
     }
-    seg_count_hits<MODE, E>(P, A, hits, e, lane_hits, hk, p, vj, tb);
+    seg_count_hits<MODE, E>(P, hits, e, lane_hits, hk, p, vj, tb);
     if (fin) {
       x = stop;
       break;
@@ -710,7 +674,7 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const VxAgg& A, 
 // nv.  Hits come out in order (listing ranks hk + i).  The padded adjacency
 // array keeps the loads inside the allocation.
 template <int MODE>
-__device__ __forceinline__ void seg_walk_short(const KParams& P, const VxAgg& A, const uint32_t* bm, uint32_t segLo,
+__device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t* bm, uint32_t segLo,
                                                uint32_t segHi, uint32_t& x, uint32_t y,
                                                uint32_t& nv, uint32_t& hk, uint32_t p, uint32_t vj,
                                                uint64_t tb, uint64_t& found) {
@@ -742,7 +706,7 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const VxAgg& A,
       const uint32_t b = w[j] - segLo;
       if (b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) {
         ++found;
-        if (MODE == M_VERTEX) vx_hit(P, A, w[j]);
+        if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[j]], 1ull);
         if (MODE == M_LIST_WRITE) emit(P, tb + hk, p, vj, w[j]);
         ++hk;
       }
@@ -761,7 +725,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
                                                                const uint32_t* __restrict__ ist,
                                                                uint32_t nh, uint32_t G, uint32_t seg_bits,
                                                                uint32_t seg_long, uint32_t seg_wide,
-                                                               uint32_t seg_tail, uint32_t agg_slots,
+                                                               uint32_t seg_tail,
                                                                const uint32_t* __restrict__ bofs,
                                                                const uint32_t* __restrict__ bnd,
                                                                uint64_t bcap) {
@@ -774,19 +738,6 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
   uint32_t* ih = nextv + SEG_ITEMS;
   uint32_t* longs = ih + SEG_ITEMS;                              // long items of the task
   uint8_t* islong = reinterpret_cast<uint8_t*>(longs + SEG_ITEMS);
-  // per-vertex mode: the third-vertex table after the item state (agg_slots
-  // a power of two, 0: none)
-  VxAgg A{nullptr, nullptr, 0u, 0};
-  if (MODE == M_VERTEX && agg_slots) {
-    A.key = reinterpret_cast<uint32_t*>(islong + SEG_ITEMS);
-    A.cnt = A.key + agg_slots;
-    A.mask = agg_slots - 1;
-    A.shift = 32 - (31 - __clz(agg_slots));
-    for (uint32_t i = threadIdx.x; i < agg_slots; i += blockDim.x) {
-      A.key[i] = EMPTY;
-      A.cnt[i] = 0;
-    }
-  }
   __shared__ uint32_t s_task, s_grp, s_pe, s_next, s_nlong;
   __shared__ uint32_t s_bound[SEG_MAXB];  // this pivot's segment bounds (when they fit)
   __shared__ unsigned long long s_hits, s_stage;
@@ -899,7 +850,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
             tb = P.toff[P.wedge[i0 + k]];
           }
           const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-          seg_walk_short<MODE>(P, A, bm, segLo, segHi, x, endp[k], nv, hk, p, vj, tb, found);
+          seg_walk_short<MODE>(P, bm, segLo, segHi, x, endp[k], nv, hk, p, vj, tb, found);
           if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
           cur[k] = x;
           nextv[k] = nv;
@@ -920,9 +871,9 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
           }
           const long long tv0 = MODE == M_TIMED ? clock64() : 0;
           if (y - x >= seg_wide)  // long remaining list: rounds of 256 entries
-            seg_walk_item<MODE, 8>(P, A, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+            seg_walk_item<MODE, 8>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
           else
-            seg_walk_item<MODE, 4>(P, A, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
+            seg_walk_item<MODE, 4>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
           if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
           __syncwarp();
           if (lane == 0) {
@@ -940,14 +891,6 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       }
       pc = pe;
       __syncthreads();
-    }
-    if (MODE == M_VERTEX && A.key) {  // flush the task's third-vertex counts
-      for (uint32_t i = threadIdx.x; i < agg_slots; i += blockDim.x) {
-        const uint32_t c = A.cnt[i];
-        if (c) atomicAdd((unsigned long long*)&P.tv[A.key[i]], (unsigned long long)c);
-        A.key[i] = EMPTY;
-        A.cnt[i] = 0;
-      }
     }
     if (MODE == M_TIMED) {
       const unsigned long long sh = s_stage / (unsigned long long)max(1u, nk);
@@ -1107,12 +1050,8 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
         k_seg_bounds<<<(unsigned)bgrid, 256, 0, s>>>(dp, nh, g->off, g->adj, seg_bits, bofs, bnd, bcap);
       AOT_TRY(last_launch());
     }
-    // the third-vertex table (per-vertex mode) when it fits beside the bitmap
-    uint32_t agg = MODE == M_VERTEX ? g->tune.vx_agg : 0u;
-    if (seg_smem_bytes(seg_bits) + 8 * (size_t)agg + SEG_STATIC_SMEM > SMEM_PER_BLOCK_MAX) agg = 0;
-    const size_t seg_smem = seg_smem_bytes(seg_bits) + 8 * (size_t)agg;
-    AOT_TRY(ensure_dyn_smem((const void*)k_seg_pivots<MODE>,
-                            seg_smem > seg_smem_bytes(SEG_BITS_MAX) ? seg_smem : seg_smem_bytes(SEG_BITS_MAX)));
+    const size_t seg_smem = seg_smem_bytes(seg_bits);
+    AOT_TRY(ensure_dyn_smem((const void*)k_seg_pivots<MODE>, seg_smem_bytes(SEG_BITS_MAX)));
     P.pivots = dp;
     P.num_pivots = nh;
     int per_sm = 0;
@@ -1120,7 +1059,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, seg_threads, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), seg_threads, seg_smem, s>>>(
-          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, agg, bofs,
+          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, bofs,
           bcap ? bnd : nullptr,
           bcap);
     AOT_TRY(last_launch());
@@ -1435,17 +1374,6 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
         t.seg_bits = sb;
         AOT_TRY(trial(t));
       }
-    }
-    if (mode == 1) {  // third-vertex table: needs segments of at most ~1 M ranks
-      const uint32_t aggs[] = {4096u, 8192u};
-      const uint32_t segs3[] = {1048576u, 786432u};
-      for (uint32_t ag : aggs)
-        for (uint32_t sb : segs3) {
-          aot_tuning t = cur;
-          t.vx_agg = ag;
-          t.seg_bits = sb;
-          AOT_TRY(trial(t));
-        }
     }
     const uint32_t tiles[] = {0u, 21u, 22u, 23u, 24u, 25u};
     for (uint32_t tb : tiles) {

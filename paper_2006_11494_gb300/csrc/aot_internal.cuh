@@ -138,7 +138,6 @@ struct Tuning {
   uint32_t tile_bits = 0;             // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
   uint32_t seg_tail = 128;            // hub_mode 0: after the first segment, items with fewer entries left walk per thread
   int seg_threads = 1024;             // hub_mode 0: threads per CTA of the segmented bitmap kernel
-  uint32_t vx_agg = 0;                // hub_mode 0, per-vertex: slots of the third-vertex table (0: off)
 };
 
 struct DevScalars {  // small device-resident scalars

@@ -129,9 +129,6 @@ def test_chunglu_full_parity():
     # later segments: long items with few entries left walked per thread
     dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=2048, seg_long=0, seg_tail=1 << 20),
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024, seg_long=64, seg_tail=200),
-    # third-vertex table in shared memory (per-vertex mode), small enough to overflow
-    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1048576, vx_agg=1024),
-    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=4096, vx_agg=8192),
     # smaller CTAs of the segmented bitmap kernel (two per SM)
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_threads=512, seg_bits=524288),
     dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_threads=256, seg_bits=2048, seg_tail=100),
