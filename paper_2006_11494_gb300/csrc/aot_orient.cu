@@ -360,7 +360,12 @@ __global__ void k_pivot_walk_big(const uint32_t* __restrict__ wofs, const uint2*
     const uint32_t p = big[k];
     const uint32_t b = wofs[p], e = wofs[p + 1];
     uint64_t w = 0;
-    for (uint32_t i = b + lane_id(); i < e; i += 32) {
+    uint32_t i = b + lane_id();
+    for (; i + 96 < e; i += 128) {  // four independent loads in flight per lane
+      const uint2 r0 = witem[i], r1 = witem[i + 32], r2 = witem[i + 64], r3 = witem[i + 96];
+      w += (uint64_t)(r0.y - r0.x) + (r1.y - r1.x) + (r2.y - r2.x) + (r3.y - r3.x);
+    }
+    for (; i < e; i += 32) {
       const uint2 r = witem[i];
       w += r.y - r.x;
     }
