@@ -209,9 +209,16 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * seg_threads (hub_mode 0): threads per CTA of the segmented bitmap kernel, a
  * multiple of 32 in [256, 1024]; with 512 and seg_bits <= 589824 two CTAs fit
  * one SM.
+ * seg_hash (hub_mode 0): after the first segment, a pivot with at most
+ * seg_hash entries of N+(p) left takes all its later segments in one pass:
+ * those entries go to a two-choice cuckoo hash table of S slots in the
+ * bitmap's shared memory (S the largest power of two <= seg_bits / 32), and
+ * every item walks the rest of its list once; 0 sweeps every segment.  A
+ * table that cannot be built (likely above S / 2 entries, certain above S)
+ * falls back to the segments; the default fills at most 3/8 of S = 32768.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
  * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
- * tile_bits 0, seg_tail 128, seg_threads 1024.
+ * tile_bits 0, seg_tail 128, seg_threads 1024, seg_hash 12288.
  * Tuning never changes results, only speed. */
 typedef struct {
   uint32_t warp_max_outdeg;
@@ -225,6 +232,7 @@ typedef struct {
   uint32_t tile_bits;
   uint32_t seg_tail;
   int32_t seg_threads;
+  uint32_t seg_hash;
 } aot_tuning;
 
 /* Work statistics of one pivot bin under the current tuning. */

@@ -89,7 +89,8 @@ class Tuning(ctypes.Structure):
                 ("hub_mode", ctypes.c_int32), ("seg_bits", ctypes.c_uint32),
                 ("seg_long", ctypes.c_uint32),
                 ("seg_wide", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32),
-                ("seg_tail", ctypes.c_uint32), ("seg_threads", ctypes.c_int32)]
+                ("seg_tail", ctypes.c_uint32), ("seg_threads", ctypes.c_int32),
+                ("seg_hash", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -412,7 +413,10 @@ class OrientedGraph:
 
     def set_tuning(self, stream=None, **kw):
         t = aot_graph_get_tuning(self.handle)
+        names = {f[0] for f in Tuning._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise TypeError("unknown tuning field %r" % k)
             setattr(t, k, v)
         aot_graph_set_tuning(self.handle, t, stream)
 

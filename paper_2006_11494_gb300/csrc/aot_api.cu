@@ -68,7 +68,8 @@ static bool tuning_valid(const aot_tuning* t) {
            t->hub_mode < 0 || t->hub_mode > 1 || t->seg_bits < 1024 || t->seg_bits > 1536u * 1024u ||
            (t->seg_bits & 31) || t->seg_long > (1u << 30) || t->seg_wide > (1u << 30) ||
            (t->tile_bits != 0 && (t->tile_bits < 16 || t->tile_bits > 31)) || t->seg_tail > (1u << 30) ||
-           t->seg_threads < 256 || t->seg_threads > 1024 || (t->seg_threads & 31));
+           t->seg_threads < 256 || t->seg_threads > 1024 || (t->seg_threads & 31) ||
+           t->seg_hash > (1u << 30));
 }
 }  // namespace aot
 
@@ -86,6 +87,7 @@ extern "C" aot_status aot_set_default_tuning(const aot_tuning* t) {
   g_default_tuning.tile_bits = t->tile_bits;
   g_default_tuning.seg_tail = t->seg_tail;
   g_default_tuning.seg_threads = t->seg_threads;
+  g_default_tuning.seg_hash = t->seg_hash;
   return AOT_OK;
 }
 
@@ -110,6 +112,7 @@ extern "C" aot_status aot_get_default_tuning(aot_tuning* t) {
   t->tile_bits = d.tile_bits;
   t->seg_tail = d.seg_tail;
   t->seg_threads = d.seg_threads;
+  t->seg_hash = d.seg_hash;
   return AOT_OK;
 }
 
@@ -194,6 +197,7 @@ extern "C" aot_status aot_graph_get_tuning(const aot_graph* g, aot_tuning* t) {
   t->tile_bits = g->tune.tile_bits;
   t->seg_tail = g->tune.seg_tail;
   t->seg_threads = g->tune.seg_threads;
+  t->seg_hash = g->tune.seg_hash;
   return AOT_OK;
 }
 
@@ -211,6 +215,7 @@ extern "C" aot_status aot_graph_set_tuning(aot_graph* g, const aot_tuning* t, ao
   g->tune.tile_bits = t->tile_bits;
   g->tune.seg_tail = t->seg_tail;
   g->tune.seg_threads = t->seg_threads;
+  g->tune.seg_hash = t->seg_hash;
   aot_status st = bin_pivots(g, reinterpret_cast<cudaStream_t>(stream));
   if (st != AOT_OK) g->tune = old;
   return st;

@@ -577,12 +577,50 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t n
   y = endp[k];
 }
 
+// Membership in the segment [segLo, segLo + 32 words) of N+(p): bit
+// b = w - segLo of the shared-memory bitmap.  Entries below segLo wrap to a
+// huge b, and every b past the bitmap reads the zero guard word, so a probe
+// needs no range test.
+struct BitProbe {
+  const uint32_t* bm;
+  uint32_t segLo, words;
+  __device__ __forceinline__ bool operator()(uint32_t w) const {
+    const uint32_t b = w - segLo;
+    const uint32_t word = bm[min(b >> 5, words)];
+    return (__funnelshift_r(word, word, b) & 1u) != 0u;
+  }
+};
+
+// Membership in the pivot's tail, the entries of N+(p) past its first
+// segment: a two-choice cuckoo table of 2^bits shared-memory slots holding
+// rank + 1 (0: empty).  Rank w sits in slot h(w) or in h(w) ^ d(w), with
+// h(w) = (w * 0x9E3779B1) >> (32 - bits) (Fibonacci hashing) and
+// d(w) = ((w * 0x85EBCA77) >> (32 - bits)) | 1 (odd, so the two slots differ
+// and each one is the other XOR d(w)).  A probe reads both slots: no loop, no
+// divergence.  Entries outside the visit (which the walks mask) may probe as
+// hits.
+__device__ __forceinline__ uint32_t tail_slot(uint32_t w, uint32_t shift) { return (w * 0x9E3779B1u) >> shift; }
+__device__ __forceinline__ uint32_t tail_step(uint32_t w, uint32_t shift) {
+  return ((w * 0x85EBCA77u) >> shift) | 1u;
+}
+struct TailProbe {
+  const uint32_t* tab;
+  uint32_t shift;
+  __device__ __forceinline__ bool operator()(uint32_t w) const {
+    const uint32_t h = tail_slot(w, shift);
+    const uint32_t a = tab[h], b = tab[h ^ tail_step(w, shift)];
+    return (a == w + 1u) | (b == w + 1u);
+  }
+};
+// Insertions that displace more keys than this give up (the table is then
+// left for the segment sweep).
+constexpr uint32_t TAIL_KICKS = 64;
+
 // One warp advances one item through the segment [segLo, segHi) in rounds of
 // 32 E entries: lane L holds the E entries at base + E L .. + E - 1 (E / 4
 // 128-bit loads, base = x rounded down to a multiple of E).  An entry w is a
-// hit iff it lies in [x, stop) and bit b = w - segLo of the bitmap is set:
-// entries below segLo wrap to a huge b, and every b past the bitmap reads the
-// zero guard word, so a probe needs no range test.  The visit ends at stop,
+// hit iff it lies in [x, stop) and probe(w) holds (every entry of the round
+// is probed: BitProbe and TailProbe take any value).  The visit ends at stop,
 // the first index >= x holding an entry >= segHi, or y.  Lists are eta-sorted,
 // so a vote on each lane's last entry tells whether stop lies in this round;
 // the vote comes before the next round's load (no round past the visit's end
@@ -592,9 +630,9 @@ __device__ __forceinline__ void seg_next_visit(const uint32_t* longs, uint32_t n
 // below x.  The adjacency array is padded so that a round starting below y
 // never reads past the allocation.
 // x: cursor (updated), hk: hits of the item so far (updated).
-template <int MODE, int E>
-__device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* bm, uint32_t seg_words,
-                                              uint32_t segLo, uint32_t segHi, uint32_t& x, uint32_t y,
+template <int MODE, int E, class Probe>
+__device__ __forceinline__ void seg_walk_item(const KParams& P, const Probe& probe, uint32_t segHi,
+                                              uint32_t& x, uint32_t y,
                                               uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
   static_assert(E == 4 || E == 8, "four or eight entries per lane");
@@ -628,11 +666,7 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
     }
     unsigned hits = 0;
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const uint32_t b = e[j] - segLo;
-      const uint32_t word = bm[min(b >> 5, seg_words)];
-      hits |= (__funnelshift_r(word, word, b) & 1u) << j;
-    }
+    for (int j = 0; j < E; ++j) hits |= (unsigned)probe(e[j]) << j;
     hits &= head;
     uint32_t stop = NONE;
     if (fin) {
@@ -667,18 +701,16 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const uint32_t* 
   if (MODE != M_COUNT && MODE != M_LIST_WRITE) hk += __reduce_add_sync(FULL, lane_hits);
 }
 
-// One thread advances one short item through the segment [segLo, segHi):
-// eight entries per step from two aligned 128-bit loads (base = x rounded
+// One thread advances one short item through the segment [segLo, segHi)
+// (hits: probe(w)): eight entries per step from two aligned 128-bit loads (base = x rounded
 // down to a multiple of 4; the entries below x are passed over), stopping at
 // the item's end y or at the first entry >= segHi, whose value is returned in
 // nv.  Hits come out in order (listing ranks hk + i).  The padded adjacency
 // array keeps the loads inside the allocation.
-template <int MODE>
-__device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t* bm, uint32_t segLo,
-                                               uint32_t segHi, uint32_t& x, uint32_t y,
-                                               uint32_t& nv, uint32_t& hk, uint32_t p, uint32_t vj,
-                                               uint64_t tb, uint64_t& found) {
-  const uint32_t width = segHi - segLo;
+template <int MODE, class Probe>
+__device__ __forceinline__ void seg_walk_short(const KParams& P, const Probe& probe, uint32_t segHi,
+                                               uint32_t& x, uint32_t y, uint32_t& nv, uint32_t& hk,
+                                               uint32_t p, uint32_t vj, uint64_t tb, uint64_t& found) {
   nv = NONE;
   while (x < y) {
     const uint32_t b0 = x & ~3u;
@@ -703,8 +735,7 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const uint32_t*
         nv = w[j];
         continue;
       }
-      const uint32_t b = w[j] - segLo;
-      if (b < width && ((bm[b >> 5] >> (b & 31)) & 1u)) {
+      if (probe(w[j])) {
         ++found;
         if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[j]], 1ull);
         if (MODE == M_LIST_WRITE) emit(P, tb + hk, p, vj, w[j]);
@@ -725,7 +756,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
                                                                const uint32_t* __restrict__ ist,
                                                                uint32_t nh, uint32_t G, uint32_t seg_bits,
                                                                uint32_t seg_long, uint32_t seg_wide,
-                                                               uint32_t seg_tail,
+                                                               uint32_t seg_tail, uint32_t seg_hash,
                                                                const uint32_t* __restrict__ bofs,
                                                                const uint32_t* __restrict__ bnd,
                                                                uint64_t bcap) {
@@ -741,10 +772,16 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
   __shared__ uint32_t s_task, s_grp, s_pe, s_next, s_nlong;
   __shared__ uint32_t s_bound[SEG_MAXB];  // this pivot's segment bounds (when they fit)
   __shared__ unsigned long long s_hits, s_stage;
+  __shared__ uint32_t s_tfail;
   const unsigned lane = lane_id(), wid = threadIdx.x >> 5;
   const uint32_t K = G * nh;
   const uint32_t ntasks = task_ofs[K];
   const bool have_bounds = bnd != nullptr && (uint64_t)bofs[nh] <= bcap;
+  // the tail table takes the bitmap's words: 2^tbits slots (two-choice
+  // cuckoo tables fill up to about half; a fuller one fails to build)
+  const uint32_t tbits = 31u - (uint32_t)__clz(seg_words);
+  const uint32_t tslots = 1u << tbits, tshift = 32u - tbits;
+  const uint32_t hcap = min(seg_hash, tslots);
   for (uint32_t i = threadIdx.x; i <= seg_words; i += blockDim.x) bm[i] = 0;  // + guard word
   uint64_t found = 0;
   while (true) {
@@ -752,6 +789,7 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       s_task = atomicAdd(&P.dev->counters[Q_SEG], 1u);
       s_hits = 0;
       s_stage = 0;
+      s_tfail = 0;
       s_nlong = 0;
     }
     __syncthreads();
@@ -820,77 +858,114 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
     const uint32_t lo_rank = P.adj[pbeg], hi_rank = P.adj[pend - 1] + 1;
     uint32_t pc = pbeg;
     __syncthreads();
+    // every item with entries in [.., segHi) advances through the segment,
+    // short ones a thread each, long ones a warp each
+    auto visit = [&](const auto& probe, uint32_t segHi, bool later_seg) {
+      for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+        if ((islong[k] && !tail_by_thread(endp[k] - cur[k], later_seg, seg_tail)) || nextv[k] >= segHi)
+          continue;
+        uint32_t x = cur[k], hk = ih[k], nv;
+        uint32_t vj = 0;
+        uint64_t tb = 0;
+        if (MODE == M_LIST_WRITE) {
+          vj = P.wvert[i0 + k];
+          tb = P.toff[P.wedge[i0 + k]];
+        }
+        const long long tv0 = MODE == M_TIMED ? clock64() : 0;
+        seg_walk_short<MODE>(P, probe, segHi, x, endp[k], nv, hk, p, vj, tb, found);
+        if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
+        cur[k] = x;
+        nextv[k] = nv;
+        ih[k] = hk;
+      }
+      const uint32_t nlong = s_nlong;
+      while (true) {
+        uint32_t k, x, y;
+        seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, later_seg, seg_tail, k, x, y);
+        if (k == NONE) break;
+        uint32_t hk = ih[k], nv;
+        uint32_t vj = 0;
+        uint64_t tb = 0;
+        if (MODE == M_LIST_WRITE) {
+          vj = P.wvert[i0 + k];
+          tb = P.toff[P.wedge[i0 + k]];
+        }
+        const long long tv0 = MODE == M_TIMED ? clock64() : 0;
+        if (y - x >= seg_wide)  // long remaining list: rounds of 256 entries
+          seg_walk_item<MODE, 8>(P, probe, segHi, x, y, hk, p, vj, tb, found, nv);
+        else
+          seg_walk_item<MODE, 4>(P, probe, segHi, x, y, hk, p, vj, tb, found, nv);
+        if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
+        __syncwarp();
+        if (lane == 0) {
+          cur[k] = x;
+          nextv[k] = nv;
+          ih[k] = hk;
+        }
+        __syncwarp();
+      }
+    };
     uint32_t sgm = 0;
+    bool tail_ok = true;  // block-uniform: may the tail table be tried?
     for (uint32_t segLo = lo_rank; segLo < hi_rank; segLo += seg_bits, ++sgm) {
-      const uint32_t segHi = min(segLo + seg_bits, hi_rank);
-      if (!use_bounds && wid == 0) {
+      uint32_t segHi = min(segLo + seg_bits, hi_rank);
+      // after the first segment, a pivot whose entries left fit the tail
+      // table takes all its later segments in one pass over a hash of them
+      bool hashed = tail_ok && sgm > 0 && segHi < hi_rank && pend - pc <= hcap;
+      const long long tset0 = MODE == M_TIMED ? clock64() : 0;
+      if (hashed) {
+        for (uint32_t k = pc + threadIdx.x; k < pend; k += blockDim.x) {
+          uint32_t key = P.adj[k] + 1u;  // distinct keys
+          uint32_t h = tail_slot(key - 1u, tshift);
+          uint32_t i = 0;
+          for (; i < TAIL_KICKS; ++i) {
+            key = atomicExch(&bm[h], key);  // place it, taking what was there
+            if (key == 0u) break;
+            h ^= tail_step(key - 1u, tshift);  // the displaced key's other slot
+          }
+          if (i == TAIL_KICKS) s_tfail = 1u;  // a key is out of the table
+        }
+        __syncthreads();
+        if (s_tfail) {  // sweep the segments instead
+          for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x) bm[i] = 0u;
+          hashed = tail_ok = false;
+        } else {
+          segHi = hi_rank;
+        }
+      }
+      if (!hashed && !use_bounds && wid == 0) {
         const uint32_t pe = warp_lower_bound(P.adj, pc, pend, segHi);
         if (lane == 0) s_pe = pe;
       }
       if (threadIdx.x == 0) s_next = 0;
       __syncthreads();
-      const uint32_t pe = use_bounds ? s_bound[sgm + 1] : s_pe;
+      const uint32_t pe = hashed ? pend : use_bounds ? s_bound[sgm + 1] : s_pe;
       if (pe > pc) {
-        const long long tset0 = MODE == M_TIMED ? clock64() : 0;
-        for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
-          const uint32_t b = P.adj[k] - segLo;
-          atomicOr(&bm[b >> 5], 1u << (b & 31));
+        if (!hashed) {
+          for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
+            const uint32_t b = P.adj[k] - segLo;
+            atomicOr(&bm[b >> 5], 1u << (b & 31));
+          }
+          __syncthreads();
         }
-        __syncthreads();
         if (MODE == M_TIMED && threadIdx.x == 0) s_stage += (unsigned long long)(clock64() - tset0) * (blockDim.x >> 5);
-        // short items: a thread each
-        for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
-          if ((islong[k] && !tail_by_thread(endp[k] - cur[k], sgm > 0, seg_tail)) || nextv[k] >= segHi)
-            continue;
-          uint32_t x = cur[k], hk = ih[k], nv;
-          uint32_t vj = 0;
-          uint64_t tb = 0;
-          if (MODE == M_LIST_WRITE) {
-            vj = P.wvert[i0 + k];
-            tb = P.toff[P.wedge[i0 + k]];
-          }
-          const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-          seg_walk_short<MODE>(P, bm, segLo, segHi, x, endp[k], nv, hk, p, vj, tb, found);
-          if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
-          cur[k] = x;
-          nextv[k] = nv;
-          ih[k] = hk;
-        }
-        // long items: a warp each
-        const uint32_t nlong = s_nlong;
-        while (true) {
-          uint32_t k, x, y;
-          seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, sgm > 0, seg_tail, k, x, y);
-          if (k == NONE) break;
-          uint32_t hk = ih[k], nv;
-          uint32_t vj = 0;
-          uint64_t tb = 0;
-          if (MODE == M_LIST_WRITE) {
-            vj = P.wvert[i0 + k];
-            tb = P.toff[P.wedge[i0 + k]];
-          }
-          const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-          if (y - x >= seg_wide)  // long remaining list: rounds of 256 entries
-            seg_walk_item<MODE, 8>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
-          else
-            seg_walk_item<MODE, 4>(P, bm, seg_words, segLo, segHi, x, y, hk, p, vj, tb, found, nv);
-          if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
-          __syncwarp();
-          if (lane == 0) {
-            cur[k] = x;
-            nextv[k] = nv;
-            ih[k] = hk;
-          }
-          __syncwarp();
-        }
+        if (hashed)
+          visit(TailProbe{bm, tshift}, segHi, true);
+        else
+          visit(BitProbe{bm, segLo, seg_words}, segHi, sgm > 0);
         __syncthreads();
-        for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
-          const uint32_t b = P.adj[k] - segLo;
-          bm[b >> 5] = 0u;
+        if (hashed) {
+          for (uint32_t i = threadIdx.x; i < tslots; i += blockDim.x) bm[i] = 0u;
+        } else {
+          for (uint32_t k = pc + threadIdx.x; k < pe; k += blockDim.x) {
+            const uint32_t b = P.adj[k] - segLo;
+            bm[b >> 5] = 0u;
+          }
         }
       }
       pc = pe;
       __syncthreads();
+      if (hashed) break;
     }
     if (MODE == M_TIMED) {
       const unsigned long long sh = s_stage / (unsigned long long)max(1u, nk);
@@ -1059,7 +1134,7 @@ static aot_status launch_bins(aot_graph* g, KParams P, cudaStream_t s) {
     AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_pivots<MODE>, seg_threads, seg_smem));
     AOT_KERNEL(mode_name<MODE>("k_seg_pivots"), s)
       k_seg_pivots<MODE><<<(unsigned)(sms * (per_sm > 0 ? per_sm : 1)), seg_threads, seg_smem, s>>>(
-          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, bofs,
+          P, task_ofs, ist, nh, G, seg_bits, g->tune.seg_long, g->tune.seg_wide, g->tune.seg_tail, g->tune.seg_hash, bofs,
           bcap ? bnd : nullptr,
           bcap);
     AOT_TRY(last_launch());
@@ -1355,17 +1430,20 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
       t.seg_wide = sw;
       AOT_TRY(trial(t));
     }
-    // segment width and the later segments' per-thread threshold interact:
-    // search them jointly
+    // segment width, the hashed tail pass and the later segments' per-thread
+    // threshold interact: search them jointly
     const uint32_t segs[] = {1572864u, 1048576u};
+    const uint32_t hashes[] = {12288u, 0u};
     const uint32_t tails[] = {64u, 96u, 128u, 160u, 192u, 256u};
-    for (uint32_t sb : segs)
-      for (uint32_t st : tails) {
-        aot_tuning t = cur;
-        t.seg_bits = sb;
-        t.seg_tail = st;
-        AOT_TRY(trial(t));
-      }
+    for (uint32_t sh : hashes)
+      for (uint32_t sb : segs)
+        for (uint32_t st : tails) {
+          aot_tuning t = cur;
+          t.seg_bits = sb;
+          t.seg_hash = sh;
+          t.seg_tail = st;
+          AOT_TRY(trial(t));
+        }
     {  // two CTAs of 512 threads per SM need segments of at most 576 K ranks
       const uint32_t segs2[] = {524288u, 589824u};
       for (uint32_t sb : segs2) {

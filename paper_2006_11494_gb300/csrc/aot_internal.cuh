@@ -138,6 +138,7 @@ struct Tuning {
   uint32_t tile_bits = 0;             // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
   uint32_t seg_tail = 128;            // hub_mode 0: after the first segment, items with fewer entries left walk per thread
   int seg_threads = 1024;             // hub_mode 0: threads per CTA of the segmented bitmap kernel
+  uint32_t seg_hash = 12288;          // hub_mode 0: pivot tails up to this many entries take one hashed pass
 };
 
 struct DevScalars {  // small device-resident scalars

@@ -132,6 +132,16 @@ def test_chunglu_full_parity():
     # smaller CTAs of the segmented bitmap kernel (two per SM)
     dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_threads=512, seg_bits=524288),
     dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_threads=256, seg_bits=2048, seg_tail=100),
+    # pivot tails past the first segment in one hashed pass: never, up to
+    # 3/8 of the table (32 to 128 slots here), up to the whole table (most
+    # builds fail and fall back to the segments), or for some pivots only;
+    # warp-wide or per-thread walks through the tail table
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024, seg_hash=0),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=1024, seg_hash=12),
+    dict(warp_max_outdeg=0, cta_max_outdeg=0, seg_bits=4096, seg_hash=1 << 30),
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=2048, seg_hash=5),
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=1024, seg_long=0, seg_wide=0, seg_tail=0),
+    dict(warp_max_outdeg=8, cta_max_outdeg=64, seg_bits=1024, seg_long=1 << 30, seg_hash=1 << 30),
     # walked-list tiles: none, several (clamped when most pivots are hubs)
     dict(tile_bits=0),
     dict(warp_max_outdeg=64, cta_max_outdeg=64, tile_bits=16),
@@ -142,14 +152,18 @@ def test_every_bin_gives_the_same_answer(tuning):
     check_full(n, s, d, tuning=tuning)
 
 
-@pytest.mark.parametrize("tile_bits,seg_bits,seg_tail", [(16, 1572864, 0), (17, 4096, 0), (0, 4096, 0),
-                                                         (0, 4096, 512), (16, 8192, 1 << 30)])
-def test_walk_tiles(tile_bits, seg_bits, seg_tail):
+@pytest.mark.parametrize("tile_bits,seg_bits,seg_tail,seg_hash", [
+    (16, 1572864, 0, 12288), (17, 4096, 0, 12288), (0, 4096, 0, 12288), (0, 4096, 512, 12288),
+    (16, 8192, 1 << 30, 12288), (0, 4096, 128, 0), (0, 16384, 128, 192), (0, 16384, 128, 100),
+    (0, 16384, 128, 1 << 30)])
+def test_walk_tiles(tile_bits, seg_bits, seg_tail, seg_hash):
     """Hub tasks handed out tile by tile of the walked out-lists (16 tiles of
-    2^16 entries at R-MAT scale 16), with one or many bitmap segments."""
+    2^16 entries at R-MAT scale 16), with one or many bitmap segments, and the
+    pivot tails past the first segment swept or hashed (tables of up to 512
+    slots at 16384-rank segments)."""
     n, s, d = gg.rmat_cfg(16, 5)
     check_full(n, s, d, tuning=dict(warp_max_outdeg=32, cta_max_outdeg=128, tile_bits=tile_bits,
-                                    seg_bits=seg_bits, seg_tail=seg_tail))
+                                    seg_bits=seg_bits, seg_tail=seg_tail, seg_hash=seg_hash))
 
 
 @pytest.mark.parametrize("case", ["rmat12", "er", "wheel", "k40", "chunglu"])
