@@ -217,7 +217,7 @@ aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, int32_t* d_o
  * table that cannot be built (likely above S / 2 entries, certain above S)
  * falls back to the segments; the default fills at most 3/8 of S = 32768.
  * Built-in defaults: warp_max_outdeg 64, cta_max_outdeg 512, cta_threads 32,
- * hub_bitmaps 32, hub_mode 0, seg_bits 1572864, seg_long 128, seg_wide 512,
+ * hub_bitmaps 32, hub_mode 0, seg_bits 1310720, seg_long 128, seg_wide 512,
  * tile_bits 0, seg_tail 128, seg_threads 1024, seg_hash 12288.
  * Tuning never changes results, only speed. */
 typedef struct {

@@ -1432,9 +1432,11 @@ extern "C" aot_status aot_tune(aot_graph* g, int32_t mode, int32_t reps, aot_tun
     }
     // segment width, the hashed tail pass and the later segments' per-thread
     // threshold interact: search them jointly
-    const uint32_t segs[] = {1572864u, 1048576u};
+    // (1310720 ranks keep the kernel's shared memory within a 196 KB carveout,
+    // leaving 60 KB of L1 for the walked lists)
+    const uint32_t segs[] = {1310720u, 1048576u, 1572864u};
     const uint32_t hashes[] = {12288u, 0u};
-    const uint32_t tails[] = {64u, 96u, 128u, 160u, 192u, 256u};
+    const uint32_t tails[] = {64u, 128u, 192u, 256u};
     for (uint32_t sh : hashes)
       for (uint32_t sb : segs)
         for (uint32_t st : tails) {

@@ -132,7 +132,7 @@ struct Tuning {
   int warp_cta_threads = 256;
   int hub_bitmaps = 32;             // concurrent hub bitmaps (n bits each)
   int hub_mode = 0;                 // 0: segmented shared-memory bitmap, 1: global bitmaps
-  uint32_t seg_bits = 1536u * 1024u;  // ranks per shared-memory bitmap segment (hub_mode 0)
+  uint32_t seg_bits = 1280u * 1024u;  // ranks per shared-memory bitmap segment (hub_mode 0)
   uint32_t seg_wide = 512;            // hub_mode 0: warp walks take rounds of 256 while this many entries remain
   uint32_t seg_long = 128;            // hub_mode 0: items this long walked warp-wide, shorter ones per thread
   uint32_t tile_bits = 0;             // hub_mode 0: tasks tile by tile of 2^tile_bits list entries (0: off)
