@@ -154,6 +154,7 @@ constexpr uint64_t LB_AGG = 1ull << 62;             // the tile's own counts
 constexpr uint64_t LB_PREFIX = 2ull << 62;          // the tile's and every earlier tile's
 constexpr uint64_t LB_VALUE = (1ull << 62) - 1;
 constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;        // polls of one predecessor (~seconds)
+constexpr int LB_BATCH = 4;                         // status words read per look-back step
 
 // Global histograms of every digit (passes x 256), per-warp copies in shared
 // memory (no lane serialisation across warps), grid-stride over the keys.
@@ -260,32 +261,9 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict_
     wh[w][t] = tot;
     tot += c;
   }
-  // publish this tile's count of digit t, then add up the earlier tiles'
+  // publish this tile's count of digit t at once (later tiles wait on it)
   uint64_t* st = status + (size_t)tile * RS_BUCKETS + t;
-  uint64_t excl = 0;
-  if (tile == 0) {
-    lb_store(st, LB_PREFIX | tot);
-  } else {
-    lb_store(st, LB_AGG | tot);
-    int64_t pt = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    while (true) {
-      const uint64_t v = lb_load(status + (size_t)pt * RS_BUCKETS + t);
-      if (!(v & ~LB_VALUE)) {  // not published yet
-        if (++spins >= LB_SPIN_LIMIT) {
-          atomicOr(err, DEVERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-        continue;
-      }
-      excl += v & LB_VALUE;
-      if ((v & ~LB_VALUE) == LB_PREFIX || pt == 0) break;
-      --pt;
-    }
-    lb_store(st, LB_PREFIX | (excl + tot));
-  }
-  gofs[t] = dbase[t] + (uint32_t)excl;
+  lb_store(st, (tile == 0 ? LB_PREFIX : LB_AGG) | tot);
   // block exclusive scan of the 256 digit totals: digit runs inside the tile
   uint32_t incl = warp_inclusive_scan(tot);
   if (lane == 31) wtot[warp] = incl;
@@ -296,6 +274,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict_
     if (w < (int)warp) wp += wtot[w];
   dstart[t] = wp + incl - tot;
   __syncthreads();
+  // the tile in digit order in shared memory (while earlier tiles publish)
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
     int64_t idx = base + r * 32 + lane;
@@ -307,6 +286,41 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict_
       if (VALS) sv[pos] = val[r];
     }
   }
+  // add up the earlier tiles' counts of digit t, LB_BATCH status words per
+  // step, back to the first inclusive prefix (tile 0 always has one)
+  uint64_t excl = 0;
+  if (tile > 0) {
+    int64_t pt = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (true) {
+      uint64_t v[LB_BATCH];
+#pragma unroll
+      for (int q = 0; q < LB_BATCH; ++q)
+        v[q] = pt - q >= 0 ? lb_load(status + (size_t)(pt - q) * RS_BUCKETS + t) : LB_PREFIX;
+      int used = 0;
+      bool done = false;
+#pragma unroll
+      for (int q = 0; q < LB_BATCH; ++q) {
+        if (done || used < q) continue;  // stopped at an earlier word
+        const uint64_t f = v[q] & ~LB_VALUE;
+        if (!f) continue;  // not published yet: poll again from here
+        excl += v[q] & LB_VALUE;
+        used = q + 1;
+        done = f == LB_PREFIX;
+      }
+      if (done) break;
+      pt -= used;
+      if (used < LB_BATCH) {  // waiting on tile pt
+        if (++spins >= LB_SPIN_LIMIT) {
+          atomicOr(err, DEVERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    lb_store(st, LB_PREFIX | (excl + tot));
+  }
+  gofs[t] = dbase[t] + (uint32_t)excl;
   __syncthreads();
   int64_t rem = N - tile_base;
   int tile_n = rem < RS_TILE ? (int)rem : RS_TILE;
@@ -316,6 +330,220 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict_
     uint32_t o = gofs[d] + (uint32_t)(j - (int)dstart[d]);
     kout[o] = k;
     if (VALS) vout[o] = sv[j];
+  }
+}
+
+// ---- TMA bulk copies into shared memory, completed on an mbarrier (PTX)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+constexpr uint32_t MB_SPIN_LIMIT = 1u << 24;  // try_wait polls of one copy
+
+// Persistent form of k_onesweep for 8-byte keys (no values): each CTA takes
+// tiles from the counter one ahead, so that the next tile's keys stream into
+// shared memory (one TMA bulk copy, two buffers) while it ranks, publishes,
+// looks back and writes the current one.  The tile is staged in digit order
+// in its own input buffer (the keys are in registers by then).  Tiles are
+// taken in increasing order and the tile held ahead is always later than the
+// one in hand, so the earliest unfinished tile is always some CTA's current
+// tile and every look-back ends.  A copy that does not complete within the
+// poll limit sets the timeout bit; the CTA then stops taking tiles.
+__global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep_tma(const uint64_t* __restrict__ kin, int64_t N,
+                                                             int64_t tiles, int shift,
+                                                             const uint32_t* __restrict__ dbase,
+                                                             uint64_t* __restrict__ status,
+                                                             unsigned int* __restrict__ tile_ctr,
+                                                             uint64_t* __restrict__ kout,
+                                                             uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t* buf = reinterpret_cast<uint64_t*>(rs_smem);  // [2][RS_TILE]
+  __shared__ uint32_t wh[RS_WARPS][RS_BUCKETS];
+  __shared__ uint32_t dstart[RS_BUCKETS];
+  __shared__ uint32_t gofs[RS_BUCKETS];
+  __shared__ uint32_t wtot[RS_WARPS];
+  __shared__ uint32_t s_tile[2];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5, t = threadIdx.x;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) wh[w][t] = 0;
+  // issue the copy of tile `tl` into buffer b (a plain arrive when there is
+  // nothing to copy, so that the buffer's phase still completes)
+  auto fetch = [&](uint32_t tl, int b) {
+    const int64_t tb = (int64_t)tl * RS_TILE;
+    const int64_t rem = N - tb;
+    const uint32_t cnt = rem < RS_TILE ? (uint32_t)rem : (uint32_t)RS_TILE;
+    const uint32_t bytes = (cnt & ~1u) * (uint32_t)sizeof(uint64_t);  // 16-byte multiple
+    if (bytes) {
+      mbar_expect_tx(&s_bar[b], bytes);
+      bulk_load(buf + (size_t)b * RS_TILE, kin + tb, bytes, &s_bar[b]);
+    } else {
+      mbar_arrive(&s_bar[b]);
+    }
+  };
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+    const uint32_t t0 = atomicAdd(tile_ctr, 1u);
+    s_tile[0] = t0;
+    if ((int64_t)t0 < tiles) fetch(t0, 0);
+  }
+  __syncthreads();
+  for (uint32_t it = 0;; ++it) {
+    const int cb = (int)(it & 1u);
+    const uint32_t tile = s_tile[cb];
+    if ((int64_t)tile >= tiles) break;
+    if (t == 0) {  // the next tile, one ahead
+      fence_proxy_async();  // earlier generic accesses of that buffer before the copy
+      const uint32_t nx = atomicAdd(tile_ctr, 1u);
+      s_tile[cb ^ 1] = nx;
+      if ((int64_t)nx < tiles) fetch(nx, cb ^ 1);
+    }
+    bool ok = false;
+    for (uint32_t sp = 0; sp < MB_SPIN_LIMIT && !ok; ++sp) ok = mbar_try_wait(&s_bar[cb], (it >> 1) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(err, DEVERR_TIMEOUT);
+      // let this CTA's copies in flight land before it exits (bounded again)
+      for (uint32_t sp = 0; sp < MB_SPIN_LIMIT && !mbar_try_wait(&s_bar[cb], (it >> 1) & 1u); ++sp) {
+      }
+      if ((int64_t)s_tile[cb ^ 1] < tiles)
+        for (uint32_t sp = 0; sp < MB_SPIN_LIMIT && !mbar_try_wait(&s_bar[cb ^ 1], ((it + 1) >> 1) & 1u); ++sp) {
+        }
+      break;
+    }
+    const uint64_t* sk = buf + (size_t)cb * RS_TILE;
+    uint64_t* so = buf + (size_t)cb * RS_TILE;
+    const int64_t tile_base = (int64_t)tile * RS_TILE;
+    const int64_t rem = N - tile_base;
+    const int tile_n = rem < RS_TILE ? (int)rem : RS_TILE;
+    const int copied = tile_n & ~1;
+    const int wbase = (int)warp * RS_WARP_KEYS;
+    uint64_t key[RS_ROUNDS];
+    uint32_t lrk[RS_ROUNDS / 2];
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      const int j = wbase + r * 32 + (int)lane;
+      key[r] = j < copied ? sk[j] : (j < tile_n ? kin[tile_base + j] : 0ull);
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      const int j = wbase + r * 32 + (int)lane;
+      const bool valid = j < tile_n;
+      unsigned d = valid ? (unsigned)((key[r] >> shift) & 0xFF) : 0x100u;
+      unsigned peers = __match_any_sync(FULL, d);
+      unsigned leader = (unsigned)(__ffs(peers) - 1);
+      uint32_t before = 0;
+      if (valid && lane == leader) {
+        before = wh[warp][d];
+        wh[warp][d] = before + (uint32_t)__popc(peers);
+      }
+      before = __shfl_sync(FULL, before, leader);
+      const uint32_t lr = before + (uint32_t)__popc(peers & lanemask_lt());
+      if (r & 1) lrk[r >> 1] |= lr << 16;
+      else lrk[r >> 1] = lr;
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      uint32_t c = wh[w][t];
+      wh[w][t] = tot;
+      tot += c;
+    }
+    uint64_t* st = status + (size_t)tile * RS_BUCKETS + t;
+    lb_store(st, (tile == 0 ? LB_PREFIX : LB_AGG) | tot);
+    uint32_t incl = warp_inclusive_scan(tot);
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    uint32_t wp = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w)
+      if (w < (int)warp) wp += wtot[w];
+    dstart[t] = wp + incl - tot;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+      const int j = wbase + r * 32 + (int)lane;
+      if (j < tile_n) {
+        unsigned d = (unsigned)((key[r] >> shift) & 0xFF);
+        const uint32_t lr = (r & 1) ? (lrk[r >> 1] >> 16) : (lrk[r >> 1] & 0xffffu);
+        so[dstart[d] + wh[warp][d] + lr] = key[r];
+      }
+    }
+    uint64_t excl = 0;
+    if (tile > 0) {
+      int64_t pt = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (true) {
+        uint64_t v[LB_BATCH];
+#pragma unroll
+        for (int q = 0; q < LB_BATCH; ++q)
+          v[q] = pt - q >= 0 ? lb_load(status + (size_t)(pt - q) * RS_BUCKETS + t) : LB_PREFIX;
+        int used = 0;
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < LB_BATCH; ++q) {
+          if (done || used < q) continue;
+          const uint64_t f = v[q] & ~LB_VALUE;
+          if (!f) continue;
+          excl += v[q] & LB_VALUE;
+          used = q + 1;
+          done = f == LB_PREFIX;
+        }
+        if (done) break;
+        pt -= used;
+        if (used < LB_BATCH) {
+          if (++spins >= LB_SPIN_LIMIT) {
+            atomicOr(err, DEVERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      lb_store(st, LB_PREFIX | (excl + tot));
+    }
+    gofs[t] = dbase[t] + (uint32_t)excl;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) wh[w][t] = 0;  // for the next tile's ranking
+    for (int j = t; j < tile_n; j += RS_THREADS) {
+      const uint64_t k = so[j];
+      const unsigned d = (unsigned)((k >> shift) & 0xFF);
+      kout[gofs[d] + (uint32_t)(j - (int)dstart[d])] = k;
+    }
+    __syncthreads();
   }
 }
 
@@ -361,12 +589,37 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
   const size_t smem = sizeof(K) * RS_TILE + (VALS ? sizeof(uint32_t) * RS_TILE : 0);
   AOT_TRY(ensure_dyn_smem((const void*)k_onesweep<K, VALS>, smem));
   AOT_TRY(prefer_max_smem((const void*)k_onesweep<K, VALS>));
+  // 8-byte keys from 16-byte aligned buffers: the persistent kernel that
+  // prefetches each CTA's next tile with a TMA bulk copy
+  constexpr bool kTmaKeys = sizeof(K) == 8 && !VALS;
+  const bool tma = kTmaKeys && ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(keys_alt)) & 15) == 0;
+  const size_t tsmem = 2 * sizeof(uint64_t) * RS_TILE;
+  int tgrid = 0;
+  if (tma) {
+    AOT_TRY(ensure_dyn_smem((const void*)k_onesweep_tma, tsmem));
+    AOT_TRY(prefer_max_smem((const void*)k_onesweep_tma));
+    int per_sm = 0;
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep_tma, RS_THREADS, tsmem));
+    int64_t g = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+    tgrid = (int)(g < tiles ? g : tiles);
+  }
   K* a = keys;
   K* b = keys_alt;
   uint32_t* va = vals;
   uint32_t* vb = vals_alt;
   for (int p = 0; p < passes; ++p) {
     AOT_CUDA(cudaMemsetAsync(status, 0, status_bytes, s));
+    if constexpr (kTmaKeys) {
+      if (tma) {
+        AOT_KERNEL("k_onesweep", s)
+          k_onesweep_tma<<<(unsigned)tgrid, RS_THREADS, tsmem, s>>>(
+              reinterpret_cast<const uint64_t*>(a), N, tiles, 8 * p, dbase + p * RS_BUCKETS, status, ctr + p,
+              reinterpret_cast<uint64_t*>(b), err);
+        AOT_TRY(last_launch());
+        K* t = a; a = b; b = t;
+        continue;
+      }
+    }
     AOT_KERNEL("k_onesweep", s)
       k_onesweep<K, VALS><<<(unsigned)tiles, RS_THREADS, smem, s>>>(a, va, N, 8 * p, dbase + p * RS_BUCKETS,
                                                                     status, ctr + p, b, vb, err);
