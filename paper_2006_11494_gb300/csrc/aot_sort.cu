@@ -199,6 +199,25 @@ __device__ __forceinline__ uint64_t lb_load(const uint64_t* p) {
 __device__ __forceinline__ void lb_store(uint64_t* p, uint64_t v) {
   atomicExch(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
+__device__ __forceinline__ uint32_t lb_load(const uint32_t* p) { return *reinterpret_cast<const volatile uint32_t*>(p); }
+__device__ __forceinline__ void lb_store(uint32_t* p, uint32_t v) { atomicExch(reinterpret_cast<unsigned int*>(p), v); }
+
+// Look-back status words of the persistent kernel: 64-bit (counts up to
+// 2^62, four words per look-back step) or, for fewer than 2^30 keys, 32-bit
+// (flag in the top two bits, count below; eight words per step, the same
+// bytes as four 64-bit ones).
+template <class SW>
+struct LbWord;
+template <>
+struct LbWord<uint64_t> {
+  static constexpr uint64_t AGG = LB_AGG, PREFIX = LB_PREFIX, VALUE = LB_VALUE;
+  static constexpr int BATCH = 4;
+};
+template <>
+struct LbWord<uint32_t> {
+  static constexpr uint32_t AGG = 1u << 30, PREFIX = 2u << 30, VALUE = (1u << 30) - 1;
+  static constexpr int BATCH = 8;
+};
 
 template <class K, bool VALS>
 __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep(const K* __restrict__ kin,
@@ -379,10 +398,11 @@ constexpr uint32_t MB_SPIN_LIMIT = 1u << 24;  // try_wait polls of one copy
 // one in hand, so the earliest unfinished tile is always some CTA's current
 // tile and every look-back ends.  A copy that does not complete within the
 // poll limit sets the timeout bit; the CTA then stops taking tiles.
+template <class SW>
 __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep_tma(const uint64_t* __restrict__ kin, int64_t N,
                                                              int64_t tiles, int shift,
                                                              const uint32_t* __restrict__ dbase,
-                                                             uint64_t* __restrict__ status,
+                                                             SW* __restrict__ status,
                                                              unsigned int* __restrict__ tile_ctr,
                                                              uint64_t* __restrict__ kout,
                                                              uint32_t* __restrict__ err) {
@@ -482,8 +502,9 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep_tma(const uint64_t* 
       wh[w][t] = tot;
       tot += c;
     }
-    uint64_t* st = status + (size_t)tile * RS_BUCKETS + t;
-    lb_store(st, (tile == 0 ? LB_PREFIX : LB_AGG) | tot);
+    using W = LbWord<SW>;
+    SW* st = status + (size_t)tile * RS_BUCKETS + t;
+    lb_store(st, (SW)((tile == 0 ? W::PREFIX : W::AGG) | tot));
     uint32_t incl = warp_inclusive_scan(tot);
     if (lane == 31) wtot[warp] = incl;
     __syncthreads();
@@ -507,24 +528,24 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep_tma(const uint64_t* 
       int64_t pt = (int64_t)tile - 1;
       uint32_t spins = 0;
       while (true) {
-        uint64_t v[LB_BATCH];
+        SW v[W::BATCH];
 #pragma unroll
-        for (int q = 0; q < LB_BATCH; ++q)
-          v[q] = pt - q >= 0 ? lb_load(status + (size_t)(pt - q) * RS_BUCKETS + t) : LB_PREFIX;
+        for (int q = 0; q < W::BATCH; ++q)
+          v[q] = pt - q >= 0 ? lb_load(status + (size_t)(pt - q) * RS_BUCKETS + t) : W::PREFIX;
         int used = 0;
         bool done = false;
 #pragma unroll
-        for (int q = 0; q < LB_BATCH; ++q) {
-          if (done || used < q) continue;
-          const uint64_t f = v[q] & ~LB_VALUE;
-          if (!f) continue;
-          excl += v[q] & LB_VALUE;
+        for (int q = 0; q < W::BATCH; ++q) {
+          if (done || used < q) continue;  // stopped at an earlier word
+          const SW f = v[q] & ~W::VALUE;
+          if (!f) continue;  // not published yet: poll again from here
+          excl += v[q] & W::VALUE;
           used = q + 1;
-          done = f == LB_PREFIX;
+          done = f == W::PREFIX;
         }
         if (done) break;
         pt -= used;
-        if (used < LB_BATCH) {
+        if (used < W::BATCH) {  // waiting on tile pt
           if (++spins >= LB_SPIN_LIMIT) {
             atomicOr(err, DEVERR_TIMEOUT);
             break;
@@ -532,7 +553,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_onesweep_tma(const uint64_t* 
           __nanosleep(64);
         }
       }
-      lb_store(st, LB_PREFIX | (excl + tot));
+      lb_store(st, (SW)(W::PREFIX | (excl + tot)));
     }
     gofs[t] = dbase[t] + (uint32_t)excl;
     __syncthreads();
@@ -596,10 +617,12 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
   const size_t tsmem = 2 * sizeof(uint64_t) * RS_TILE;
   int tgrid = 0;
   if (tma) {
-    AOT_TRY(ensure_dyn_smem((const void*)k_onesweep_tma, tsmem));
-    AOT_TRY(prefer_max_smem((const void*)k_onesweep_tma));
+    for (const void* f : {(const void*)k_onesweep_tma<uint32_t>, (const void*)k_onesweep_tma<uint64_t>}) {
+      AOT_TRY(ensure_dyn_smem(f, tsmem));
+      AOT_TRY(prefer_max_smem(f));
+    }
     int per_sm = 0;
-    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep_tma, RS_THREADS, tsmem));
+    AOT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep_tma<uint64_t>, RS_THREADS, tsmem));
     int64_t g = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
     tgrid = (int)(g < tiles ? g : tiles);
   }
@@ -611,10 +634,16 @@ static aot_status radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
     AOT_CUDA(cudaMemsetAsync(status, 0, status_bytes, s));
     if constexpr (kTmaKeys) {
       if (tma) {
-        AOT_KERNEL("k_onesweep", s)
-          k_onesweep_tma<<<(unsigned)tgrid, RS_THREADS, tsmem, s>>>(
-              reinterpret_cast<const uint64_t*>(a), N, tiles, 8 * p, dbase + p * RS_BUCKETS, status, ctr + p,
-              reinterpret_cast<uint64_t*>(b), err);
+        AOT_KERNEL("k_onesweep", s) {
+          const uint64_t* ka = reinterpret_cast<const uint64_t*>(a);
+          uint64_t* kb = reinterpret_cast<uint64_t*>(b);
+          if (N < (int64_t)LbWord<uint32_t>::VALUE)  // every count fits 30 bits
+            k_onesweep_tma<uint32_t><<<(unsigned)tgrid, RS_THREADS, tsmem, s>>>(
+                ka, N, tiles, 8 * p, dbase + p * RS_BUCKETS, reinterpret_cast<uint32_t*>(status), ctr + p, kb, err);
+          else
+            k_onesweep_tma<uint64_t><<<(unsigned)tgrid, RS_THREADS, tsmem, s>>>(
+                ka, N, tiles, 8 * p, dbase + p * RS_BUCKETS, status, ctr + p, kb, err);
+        }
         AOT_TRY(last_launch());
         K* t = a; a = b; b = t;
         continue;
