@@ -457,21 +457,29 @@ def run_ours(a):
     if not a.no_extras:
         extras["variants"] = variants(aot, src, dst, n, ws, stream, phase_ms, T)
 
-    # end to end: pinned host edge list in, per-vertex counts out, every step.
-    # Each step's input is copied on a copy stream into one of two device
-    # buffers while the previous step computes (a user's pipeline); the serial
-    # form (copy, then compute) is reported beside it.
+    # end to end: pinned host edge list in, per-vertex counts out, every step,
+    # in two pipelines a user may run: each step's input copied on a copy
+    # stream into one of two device buffers while the previous step computes,
+    # or copy then compute.  The host-to-device copy runs at very different
+    # speeds beside the bandwidth-bound count kernel from one GPU machine to the
+    # next, so either can be the faster: the value is the faster one, and both
+    # times are in the line.
     e2e = None
     if not a.no_e2e:
-        e_ms, e_wall = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream,
+        o_ms, o_wall = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream,
                                 a.steps, True, barrier)
-        s_ms, _ = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream, a.steps,
-                           False, barrier)
-        e_ms = max_over_ranks(e_ms, dev)
+        s_ms, s_wall = e2e_loop(torch, aot, step, src, dst, h_src, h_dst, counts, h_counts, stream, a.steps,
+                                False, barrier)
+        o_ms = max_over_ranks(o_ms, dev)
+        s_ms = max_over_ranks(s_ms, dev)
+        overlap_wins = o_ms <= s_ms
+        e_ms = o_ms if overlap_wins else s_ms
         e2e = {"value": replica_value(info["m"], e_ms, world), "unit": UNIT, "ms_per_step": e_ms,
-               "wall_ms_per_step": e_wall, "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n,
-               "copies": "overlapped with the previous step (two input buffers, a copy stream)",
-               "serial_ms_per_step": s_ms}
+               "wall_ms_per_step": o_wall if overlap_wins else s_wall,
+               "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * n,
+               "copies": ("overlapped with the previous step (two input buffers, a copy stream)" if overlap_wins
+                          else "serial: copy in, then orient + count, then copy out"),
+               "overlapped_ms_per_step": o_ms, "serial_ms_per_step": s_ms}
 
     if rank != 0:
         return
