@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) k_warp_pivots(KParams P, uint32_t ts_max,
     if (idx >= P.num_pivots) break;
     const uint32_t p = P.pivots[idx];
     if (P.rprobe && P.rprobe[p] == 0) continue;  // every item of p takes another route
+    if (MODE == M_LIST_WRITE && !list_window_overlaps(P, P.wofs[p], P.wofs[p + 1])) continue;
     const uint32_t b = P.off[p], d = P.off[p + 1] - b;
     const long long tst0 = MODE == M_TIMED ? clock64() : 0;
     uint32_t ts = 32;
@@ -282,7 +283,8 @@ __global__ void __launch_bounds__(1024, 1) k_cta_pivots(KParams P, uint32_t ts_m
     const uint32_t idx = s_idx;
     if (idx >= P.num_pivots) break;
     const uint32_t p = P.pivots[idx];
-    if (P.rprobe && P.rprobe[p] == 0) {  // every item of p takes another route
+    if ((P.rprobe && P.rprobe[p] == 0) ||  // every item of p takes another route
+        (MODE == M_LIST_WRITE && !list_window_overlaps(P, P.wofs[p], P.wofs[p + 1]))) {
       __syncthreads();
       continue;
     }
@@ -825,6 +827,10 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
       for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_bound[t] = bnd[bofs[h] + t];
     const uint32_t i0 = group_bound(ist, P.wofs, p, h, nh, G, grp) + (task - task_ofs[kg]) * SEG_ITEMS;
     const uint32_t i1 = min(i0 + SEG_ITEMS, group_bound(ist, P.wofs, p, h, nh, G, grp + 1));
+    if (MODE == M_LIST_WRITE && !list_window_overlaps(P, i0, i1)) {  // nothing of this task in the window
+      __syncthreads();
+      continue;
+    }
     const uint32_t nk = i1 - i0;
     int live = 0;  // does any item of this task walk anything?
     for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
@@ -1210,6 +1216,7 @@ static KParams base_params(aot_graph* g) {
   P.route = g->routed ? g->route : nullptr;
   P.rprobe = g->routed ? g->rprobe : nullptr;
   P.cyc = nullptr;
+  P.lblk = nullptr;
   return P;
 }
 
@@ -1239,6 +1246,45 @@ static aot_status run_mode(aot_graph* g, aot_route route, KParams P, cudaStream_
   P.rprobe = g->routed ? g->rprobe : nullptr;
   AOT_TRY(launch_bins<MODE>(g, P, s));
   return launch_ep<MODE>(g, P, s);
+}
+
+// Listing block ranges (see LIST_BLOCK): a CTA per block of work items.
+__global__ void __launch_bounds__(256) k_list_blocks(const uint32_t* __restrict__ wedge,
+                                                     const uint64_t* __restrict__ toff, uint32_t items,
+                                                     uint32_t nblk, uint64_t* __restrict__ lblk) {
+  __shared__ unsigned long long s_lo, s_hi;
+  for (uint32_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    if (threadIdx.x == 0) {
+      s_lo = ~0ull;
+      s_hi = 0;
+    }
+    __syncthreads();
+    unsigned long long lo = ~0ull, hi = 0;
+    const uint32_t i0 = blk * LIST_BLOCK, i1 = min(i0 + LIST_BLOCK, items);
+    for (uint32_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const uint32_t e = wedge[i];
+      const unsigned long long a = toff[e], b = toff[e + 1];
+      if (a < b) {
+        lo = min(lo, a);
+        hi = max(hi, b);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+      hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    if (lane_id() == 0) {
+      atomicMin(&s_lo, lo);
+      atomicMax(&s_hi, hi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      lblk[2 * (size_t)blk] = s_lo;
+      lblk[2 * (size_t)blk + 1] = s_hi;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void k_gather_counts(const uint64_t* __restrict__ tv, const int32_t* __restrict__ rank,
@@ -1320,6 +1366,18 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
       AOT_CUDA(cudaMemsetAsync(g->tcnt, 0, sizeof(uint32_t) * g->m, s));
       AOT_TRY(run_mode<M_LIST_COUNT>(g, route, base_params(g), s));
       AOT_TRY(scan_u32_u64(g->tcnt, g->toff, g->m, g->scan_tmp, s));
+      // block ranges in tcnt's words, dead after the scan (a 256-byte piece
+      // of at least 4 m bytes holds the 16 ceil(m / LIST_BLOCK) it needs)
+      const uint64_t nblk = ((uint64_t)g->m + LIST_BLOCK - 1) / LIST_BLOCK;
+      const uint64_t room = ((uint64_t)g->m * sizeof(uint32_t) + 255) & ~(uint64_t)255;
+      g->lblk = nullptr;
+      if (16 * nblk <= room) {
+        g->lblk = reinterpret_cast<uint64_t*>(g->tcnt);
+        unsigned grid = (unsigned)(nblk < (uint64_t)sm_count() * 16 ? nblk : (uint64_t)sm_count() * 16);
+        AOT_KERNEL("k_list_blocks", s)
+          k_list_blocks<<<grid, 256, 0, s>>>(g->wedge, g->toff, (uint32_t)g->m, (uint32_t)nblk, g->lblk);
+        AOT_TRY(last_launch());
+      }
       unsigned long long t = 0;
       AOT_CUDA(cudaMemcpyAsync(&t, g->toff + g->m, sizeof(t), cudaMemcpyDeviceToHost, s));
       AOT_CUDA(cudaStreamSynchronize(s));
@@ -1336,6 +1394,7 @@ extern "C" aot_status aot_list(aot_graph* g, aot_route route, uint64_t cursor, i
     P.out = d_out;
     P.cursor = cursor;
     P.cap = k;
+    P.lblk = g->lblk;
     AOT_TRY(reset_scalars(g, s));
     AOT_TRY(run_mode<M_LIST_WRITE>(g, route, P, s));
     AOT_CUDA(cudaStreamSynchronize(s));

@@ -191,6 +191,7 @@ struct aot_graph {
   aot::DevScalars* dev = nullptr;
   bool has_list = false;
   bool list_ready = false;
+  uint64_t* lblk = nullptr;       // listing block ranges (in tcnt's words once the offsets are scanned)
   uint64_t list_total = 0;
   // bins (host copy of counts), valid for the thresholds in `binned_for`
   uint32_t bin_count[aot::NUM_BINS] = {0, 0, 0};

@@ -28,7 +28,26 @@ struct KParams {
   const uint8_t* route;    // variant per item (nullptr: every item probes)
   uint32_t* cyc;           // M_TIMED: cycles per oriented edge
   const uint32_t* rprobe;  // probe items per pivot (nullptr: all items)
+  const uint64_t* lblk;    // listing: output range per block of LIST_BLOCK items (nullptr: none)
 };
+
+// Work items per listing block: lblk[2 b] and lblk[2 b + 1] are the smallest
+// first and the largest end triangle number of the items
+// [b LIST_BLOCK, (b + 1) LIST_BLOCK) that have a triangle ([2^64 - 1, 0) when
+// none has).  Items are stored pivot by pivot in rank order, a pivot's
+// positive items in out-list order, so a block's range is narrow.
+constexpr uint32_t LIST_BLOCK = 1536;
+
+// Can any item of [i0, i1) write a triangle of the listing window?  (Always
+// true without block ranges; a conservative test otherwise.)
+__device__ __forceinline__ bool list_window_overlaps(const KParams& P, uint32_t i0, uint32_t i1) {
+  if (!P.lblk) return true;
+  if (i0 >= i1) return false;
+  const uint64_t w0 = P.cursor, w1 = P.cursor + P.cap;
+  for (uint32_t b = i0 / LIST_BLOCK; b <= (i1 - 1) / LIST_BLOCK; ++b)
+    if (P.lblk[2 * (size_t)b + 1] > w0 && P.lblk[2 * (size_t)b] < w1) return true;
+  return false;
+}
 
 // Listing output: triangle number idx, if it falls in the window, as
 // (x, y, w) in original ids with eta(x) < eta(y) < eta(w).
