@@ -43,3 +43,12 @@ def test_recorded_entry_names_existing_sources():
         assert e["bytes"] > 0 and e["tuning"]
         for rel in e["sources"]:
             assert (bench.os.path.exists(bench.os.path.join(bench.ROOT, rel))), rel
+
+
+def test_recorded_tuning_has_every_tuning_field():
+    """A recorded entry can only match the tuning the autotuner returns when
+    it names exactly the library's tuning fields."""
+    from paper_2006_11494_gb300 import Tuning
+    fields = {name for name, _ in Tuning._fields_}
+    for e in bench.MEASURED_TRAFFIC.values():
+        assert set(e["tuning"]) == fields
