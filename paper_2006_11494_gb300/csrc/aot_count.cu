@@ -66,10 +66,12 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
   uint64_t tbase = 0;
   if (MODE != M_COUNT && has) vert = P.wvert[it];
   if (MODE >= M_LIST_COUNT && has) edge = P.wedge[it];
+  uint2 ends = make_uint2(0u, 0u);  // listing: this lane's item's first two ids
   if (MODE == M_LIST_WRITE && has) {
     uint64_t a = P.toff[edge], b = P.toff[edge + 1];
     if (a == b || b <= P.cursor || a >= P.cursor + P.cap) r.y = r.x;  // nothing in the window
     tbase = a;
+    if (r.x < r.y) ends = emit_ends(P, p, vert);
   }
   uint32_t len = r.y - r.x;
   uint32_t ihits = 0;  // hits of the item held by this lane
@@ -83,10 +85,10 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
     longm &= longm - 1;
     const long long t0 = MODE == M_TIMED ? clock64() : 0;
     const uint32_t x = __shfl_sync(FULL, r.x, j), y = __shfl_sync(FULL, r.y, j);
-    uint32_t vj = 0;
+    uint2 ej = make_uint2(0u, 0u);
     uint64_t tb = 0;
     if (MODE == M_LIST_WRITE) {
-      vj = __shfl_sync(FULL, vert, j);
+      ej = make_uint2(__shfl_sync(FULL, ends.x, j), __shfl_sync(FULL, ends.y, j));
       tb = ((uint64_t)__shfl_sync(FULL, (uint32_t)(tbase >> 32), j) << 32) |
            __shfl_sync(FULL, (uint32_t)tbase, j);
     }
@@ -107,7 +109,7 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
         if (hit[u]) {
           ++my;
           if (MODE == M_VERTEX) on_w(w[u], slot[u]);
-          if (MODE == M_LIST_WRITE) emit(P, tb + h + (uint32_t)__popc(hm & lanemask_lt()), p, vj, w[u]);
+          if (MODE == M_LIST_WRITE) emit(P, tb + h + (uint32_t)__popc(hm & lanemask_lt()), ej, w[u]);
         }
         h += (uint32_t)__popc(hm);
       }
@@ -147,10 +149,10 @@ __device__ __forceinline__ uint32_t walk_chunk(const KParams& P, uint32_t p, uin
       const unsigned peers = __match_any_sync(FULL, j);
       const uint32_t tb_lo = __shfl_sync(FULL, (uint32_t)tbase, j);
       const uint32_t tb_hi = __shfl_sync(FULL, (uint32_t)(tbase >> 32), j);
-      const uint32_t vj = __shfl_sync(FULL, vert, j);
+      const uint2 ej = make_uint2(__shfl_sync(FULL, ends.x, j), __shfl_sync(FULL, ends.y, j));
       if (hit)
         emit(P, (((uint64_t)tb_hi << 32) | tb_lo) + prev + (uint32_t)__popc(hm & peers & lanemask_lt()),
-             p, vj, w);
+             ej, w);
     }
     if (MODE != M_COUNT) {
       const int64_t lo = (int64_t)excl - (int64_t)q0, hi = (int64_t)incl - (int64_t)q0;
@@ -530,8 +532,8 @@ __global__ void k_seg_bounds(const uint32_t* __restrict__ pivots, uint32_t nh,
 // third vertices (listing ranks follow the warp's lane order).
 template <int MODE, int E>
 __device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, const uint32_t (&e)[E],
-                                               uint32_t& lane_hits, uint32_t& hk, uint32_t p,
-                                               uint32_t vj, uint64_t tb) {
+                                               uint32_t& lane_hits, uint32_t& hk, uint2 ends,
+                                               uint64_t tb) {
   const uint32_t c = (uint32_t)__popc(hits);
   lane_hits += c;
   if (MODE == M_VERTEX) {
@@ -544,7 +546,7 @@ __device__ __forceinline__ void seg_count_hits(const KParams& P, unsigned hits, 
     uint64_t r = tb + hk + (incl - c);
 #pragma unroll
     for (int j = 0; j < E; ++j)
-      if (hits & (1u << j)) emit(P, r++, p, vj, e[j]);
+      if (hits & (1u << j)) emit(P, r++, ends, e[j]);
     hk += __shfl_sync(FULL, incl, 31);
   }
 }
@@ -635,7 +637,7 @@ constexpr uint32_t TAIL_KICKS = 64;
 template <int MODE, int E, class Probe>
 __device__ __forceinline__ void seg_walk_item(const KParams& P, const Probe& probe, uint32_t segHi,
                                               uint32_t& x, uint32_t y,
-                                              uint32_t& hk, uint32_t p, uint32_t vj, uint64_t tb,
+                                              uint32_t& hk, uint2 ends, uint64_t tb,
                                               uint64_t& found, uint32_t& next_val) {
   static_assert(E == 4 || E == 8, "four or eight entries per lane");
   constexpr unsigned ALL = (1u << E) - 1u;
@@ -690,7 +692,7 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const Probe& pro
       const uint32_t val = __shfl_sync(FULL, at, (rel / E) & 31u);
       next_val = stop < y ? val : NONE;
     }
-    seg_count_hits<MODE, E>(P, hits, e, lane_hits, hk, p, vj, tb);
+    seg_count_hits<MODE, E>(P, hits, e, lane_hits, hk, ends, tb);
     if (fin) {
       x = stop;
       break;
@@ -712,7 +714,7 @@ __device__ __forceinline__ void seg_walk_item(const KParams& P, const Probe& pro
 template <int MODE, class Probe>
 __device__ __forceinline__ void seg_walk_short(const KParams& P, const Probe& probe, uint32_t segHi,
                                                uint32_t& x, uint32_t y, uint32_t& nv, uint32_t& hk,
-                                               uint32_t p, uint32_t vj, uint64_t tb, uint64_t& found) {
+                                               uint2 ends, uint64_t tb, uint64_t& found) {
   nv = NONE;
   while (x < y) {
     const uint32_t b0 = x & ~3u;
@@ -740,7 +742,7 @@ __device__ __forceinline__ void seg_walk_short(const KParams& P, const Probe& pr
       if (probe(w[j])) {
         ++found;
         if (MODE == M_VERTEX) atomicAdd((unsigned long long*)&P.tv[w[j]], 1ull);
-        if (MODE == M_LIST_WRITE) emit(P, tb + hk, p, vj, w[j]);
+        if (MODE == M_LIST_WRITE) emit(P, tb + hk, ends, w[j]);
         ++hk;
       }
     }
@@ -871,14 +873,14 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         if ((islong[k] && !tail_by_thread(endp[k] - cur[k], later_seg, seg_tail)) || nextv[k] >= segHi)
           continue;
         uint32_t x = cur[k], hk = ih[k], nv;
-        uint32_t vj = 0;
+        uint2 ends = make_uint2(0u, 0u);
         uint64_t tb = 0;
         if (MODE == M_LIST_WRITE) {
-          vj = P.wvert[i0 + k];
+          ends = emit_ends(P, p, P.wvert[i0 + k]);
           tb = P.toff[P.wedge[i0 + k]];
         }
         const long long tv0 = MODE == M_TIMED ? clock64() : 0;
-        seg_walk_short<MODE>(P, probe, segHi, x, endp[k], nv, hk, p, vj, tb, found);
+        seg_walk_short<MODE>(P, probe, segHi, x, endp[k], nv, hk, ends, tb, found);
         if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
         cur[k] = x;
         nextv[k] = nv;
@@ -890,17 +892,17 @@ __global__ void __launch_bounds__(SEG_THREADS, 1) k_seg_pivots(KParams P, const 
         seg_next_visit(longs, nlong, &s_next, nextv, cur, endp, segHi, later_seg, seg_tail, k, x, y);
         if (k == NONE) break;
         uint32_t hk = ih[k], nv;
-        uint32_t vj = 0;
+        uint2 ends = make_uint2(0u, 0u);
         uint64_t tb = 0;
         if (MODE == M_LIST_WRITE) {
-          vj = P.wvert[i0 + k];
+          ends = emit_ends(P, p, P.wvert[i0 + k]);
           tb = P.toff[P.wedge[i0 + k]];
         }
         const long long tv0 = MODE == M_TIMED ? clock64() : 0;
         if (y - x >= seg_wide)  // long remaining list: rounds of 256 entries
-          seg_walk_item<MODE, 8>(P, probe, segHi, x, y, hk, p, vj, tb, found, nv);
+          seg_walk_item<MODE, 8>(P, probe, segHi, x, y, hk, ends, tb, found, nv);
         else
-          seg_walk_item<MODE, 4>(P, probe, segHi, x, y, hk, p, vj, tb, found, nv);
+          seg_walk_item<MODE, 4>(P, probe, segHi, x, y, hk, ends, tb, found, nv);
         if (MODE == M_TIMED) hk = ih[k] + sat_cycles(clock64() - tv0);  // ih holds cycles here
         __syncwarp();
         if (lane == 0) {

@@ -50,13 +50,17 @@ __device__ __forceinline__ bool list_window_overlaps(const KParams& P, uint32_t 
 }
 
 // Listing output: triangle number idx, if it falls in the window, as
-// (x, y, w) in original ids with eta(x) < eta(y) < eta(w).
-__device__ __forceinline__ void emit(const KParams& P, uint64_t idx, uint32_t p, uint32_t v,
-                                     uint32_t w) {
+// (x, y, w) in original ids with eta(x) < eta(y) < eta(w).  (x, y) are the
+// item's pivot and walked vertex, the same for all its triangles:
+// emit_ends gives them once per item.
+__device__ __forceinline__ uint2 emit_ends(const KParams& P, uint32_t p, uint32_t v) {
+  return make_uint2((uint32_t)P.perm[p < v ? p : v], (uint32_t)P.perm[p < v ? v : p]);
+}
+__device__ __forceinline__ void emit(const KParams& P, uint64_t idx, uint2 ends, uint32_t w) {
   if (idx >= P.cursor && idx < P.cursor + P.cap) {
     int32_t* o = P.out + 3 * (idx - P.cursor);
-    o[0] = P.perm[p < v ? p : v];
-    o[1] = P.perm[p < v ? v : p];
+    o[0] = (int32_t)ends.x;
+    o[1] = (int32_t)ends.y;
     o[2] = P.perm[w];
   }
 }

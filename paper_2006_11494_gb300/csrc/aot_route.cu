@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
       tb = a;
     }
     const uint32_t pb = P.off[p], pe = P.off[p + 1];
+    const uint2 ends = MODE == M_LIST_WRITE ? emit_ends(P, p, vert) : make_uint2(0u, 0u);
     uint32_t h = 0;  // hits of this item (warp-uniform after reductions)
     if (x < y && pb < pe) {
       if (route[it] == V_BSEARCH) {
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
           const unsigned hm = __ballot_sync(FULL, hit);
           if (hit) {
             ep_hit<MODE>(P, w);
-            if (MODE == M_LIST_WRITE) emit(P, tb + h + (uint32_t)__popc(hm & lanemask_lt()), p, vert, w);
+            if (MODE == M_LIST_WRITE) emit(P, tb + h + (uint32_t)__popc(hm & lanemask_lt()), ends, w);
           }
           h += (uint32_t)__popc(hm);
         }
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) k_items_ep(KParams P, const uint2* __rest
             const uint32_t av = __ldg(P.adj + a);
             uint32_t bv = __ldg(P.adj + bpos);
             while (bv < av && ++bpos < pe) bv = __ldg(P.adj + bpos);
-            if (bpos < pe && bv == av) emit(P, idx++, p, vert, av);
+            if (bpos < pe && bv == av) emit(P, idx++, ends, av);
           }
         }
         h = __shfl_sync(FULL, incl, 31);
